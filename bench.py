@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the EXACT-MPPI hot path on GB300.
+
+Headline workload: the batched signed-distance microbenchmark -- 16,384
+poses x 8,192 obstacle points against a random 32-vertex simple polygon,
+producing the full 134,217,728-entry signed-distance matrix plus the per-pose
+minimum and argmin (one exact_sdf_batch call per step).  Metric: point-edge
+evaluations per second over the whole job.
+
+Also measured in the same run (unless --no-extra): the plain MPPI control
+cycle (K=256, T=20, N=512, L footprint) and the forklift cycle (K=2048, T=40,
+N=4,096, 3-box cover), each replayed from a CUDA graph.
+
+--impl reference times the FP64 CPU oracle (the parity reference, untuned)
+on a bounded sample of the same workload on the host cores.
+
+Multi-GPU (torchrun, one process per GPU): every rank runs its own replica of
+the workload (weak scaling, no data-path collective); the per-step time is
+the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_POSES, N_POINTS, N_VERTS = 16384, 8192, 32
+FLOPS_PER_POINT_EDGE = 17      # canonical count, FMA = 2
+FLOPS_PER_POINT_BOX = 12
+L2_BYTES = 129 * 1024 * 1024
+
+
+def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU oracle arm
+def oracle_sdf_sample(n_poses_sample: int, threads: int | None = None):
+    """Time the FP64 oracle on the first n poses x all points x 32-gon."""
+    import numpy as np
+    import oracle
+    import synth
+    w = synth.sdf_microbench(seed=0)
+    if threads:
+        oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    oracle.sdf_batch(w["points"], w["poses"][:n_poses_sample], w["kind"], w["fp"], want_dist=True)
+    dt = time.perf_counter() - t0
+    return n_poses_sample * N_POINTS * N_VERTS / dt, dt
+
+
+def calibrate_oracle(target_s: float):
+    """Number of poses for which the oracle takes about target_s seconds."""
+    import oracle
+    oracle.build()
+    oracle_sdf_sample(8)                      # thread pool start-up
+    _, t = oracle_sdf_sample(64)
+    return int(max(8, min(N_POSES, 64 * target_s / max(t, 1e-6))))
+
+
+def cpu_baseline(target_s: float = 10.0) -> dict:
+    import oracle
+    n = calibrate_oracle(target_s)
+    v, dt = oracle_sdf_sample(n)
+    cores = oracle.max_threads()
+    return {"value": v, "unit": "point-edge evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {N_POSES} poses x {N_POINTS} points x {N_VERTS}-vertex polygon, full distance "
+                      f"matrix + min/argmin, float64, OpenMP over poses ({cores} threads), {dt:.1f} s",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    n = calibrate_oracle(1.5)
+    for _ in range(args.warmup):
+        oracle_sdf_sample(n)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sdf_sample(n)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * n * N_POINTS * N_VERTS / total
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": "SDF point-edge evals/s", "value": value, "unit": "point-edge evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sdf_microbench sample: {n} of {N_POSES} poses x {N_POINTS} points x "
+                                   f"{N_VERTS}-vertex polygon per step (CPU oracle)",
+                       "poses_per_step": n, "points": N_POINTS, "edges": N_VERTS},
+            "cpu_baseline": {"value": value, "unit": "point-edge evals/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} poses x {N_POINTS} points x {N_VERTS} edges per step, float64"},
+            "e2e": {"value": value, "unit": "point-edge evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def time_graph(torch, fn, iters: int, warm: int = 3):
+    """Capture fn() in a CUDA graph and time `iters` replays with events."""
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(warm):
+            fn()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    for _ in range(warm):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / iters
+
+
+def mppi_extra(torch, ex, dev):
+    import synth
+    out = {}
+    ctx = ex.Context()
+    for name, make, iters in (("plain_step", lambda: synth.plain_step(0), 2000),
+                              ("forklift", lambda: synth.forklift(0), 200)):
+        s = make()
+        p = s["params"]
+        fp = ex.Footprint(s["kind"], s["fp"])
+        t = {k: torch.from_numpy(v).to(dev) for k, v in s.items()
+             if k in ("q0", "cloud", "waypoints", "U", "eps") and v is not None}
+        mask = torch.from_numpy(s["mask"]).to(dev) if s["mask"] is not None else None
+        U = t["U"].clone()
+        ctx.reserve(0, p["K"], p["T"])
+        outs = {}
+
+        def step():
+            outs.update(ex.mppi_step(ctx, t["q0"], t["cloud"], t["waypoints"], U, t["eps"], fp, p, mask=mask,
+                                     out=outs))
+
+        step()
+        ms = time_graph(torch, step, iters)
+        N = s["cloud"].shape[0]
+        per_step = p["K"] * p["T"] * N * (s["fp"].shape[0] if s["kind"] == synth.POLYGON else s["fp"].shape[0])
+        flops = per_step * (FLOPS_PER_POINT_EDGE if s["kind"] == synth.POLYGON else FLOPS_PER_POINT_BOX)
+        out[name] = {"steps_per_s": 1e3 / ms, "us_per_step": 1e3 * ms, "K": p["K"], "T": p["T"], "N": N,
+                     "footprint": ("polygon" if s["kind"] == synth.POLYGON else "rects") + f"x{s['fp'].shape[0]}",
+                     "evals_per_step": per_step, "counted_tflops": flops / (ms * 1e-3) / 1e12,
+                     "launches_per_step": 3, "timing": "CUDA graph replay, events, inputs L2-resident"}
+    return out
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2605_29663_gb300 as ex
+    import synth
+    from paper_2605_29663_gb300 import build as _build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    else:
+        dist = None
+
+    if rank == 0:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    _build.build()   # no-op once built
+    ex.load()
+
+    w = synth.sdf_microbench(seed=rank)
+    fp = ex.Footprint(w["kind"], w["fp"])
+    ctx = ex.Context()
+    pts = torch.from_numpy(w["points"]).to(dev)
+    poses = torch.from_numpy(w["poses"]).to(dev)
+    d = torch.empty((N_POSES, N_POINTS), dtype=torch.float32, device=dev)
+    m = torch.empty(N_POSES, dtype=torch.float32, device=dev)
+    a = torch.empty(N_POSES, dtype=torch.int32, device=dev)
+    out = {"dist": d, "dmin": m, "argmin": a}
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        ex.sdf_batch(pts, poses, fp, ctx=ctx, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()                  # L2 flushed between timed iterations (outside the events)
+            starts[i].record()
+            step()
+            ends[i].record()
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(per) / len(per)
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    evals = N_POSES * N_POINTS * N_VERTS
+    value = world * evals / (ms * 1e-3)
+
+    # end to end through the public call with host buffers: H2D of the step's
+    # inputs from pinned memory, the call, D2H of the per-pose min / argmin
+    h_pts = torch.from_numpy(w["points"]).pin_memory()
+    h_poses = torch.from_numpy(w["poses"]).pin_memory()
+    h_m = torch.empty(N_POSES, dtype=torch.float32).pin_memory()
+    h_a = torch.empty(N_POSES, dtype=torch.int32).pin_memory()
+    e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(e_steps):
+        pts.copy_(h_pts, non_blocking=True)
+        poses.copy_(h_poses, non_blocking=True)
+        ex.sdf_batch(pts, poses, fp, ctx=ctx, out=out)
+        h_m.copy_(m, non_blocking=True)
+        h_a.copy_(a, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+    e2e_val = world * evals / (e2e_ms * 1e-3)
+    h2d = h_pts.numel() * 4 + h_poses.numel() * 4
+    d2h = h_m.numel() * 4 + h_a.numel() * 4
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    clocks = clk.summary()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_peak_tflops(sm_max)
+    achieved = FLOPS_PER_POINT_EDGE * evals / (ms * 1e-3) / 1e12
+    traffic = None
+    line = {
+        "metric": "SDF point-edge evals/s", "value": value, "unit": "point-edge evals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"sdf_microbench: {N_POSES} poses x {N_POINTS} points x {N_VERTS}-vertex star "
+                               "polygon, full signed-distance matrix + per-pose min/argmin",
+                   "poses": N_POSES, "points": N_POINTS, "edges": N_VERTS, "seed": "rank",
+                   "l2": "flushed (2x L2 zero-fill) between timed iterations", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "sdf_batch_kernel<PolyC<32>, true>",
+                     "flops_per_launch": FLOPS_PER_POINT_EDGE * evals,
+                     "peak_basis": f"152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_max:.0f} MHz max SM clock "
+                                   "(derived; MEASURED_PEAKS.json carries only HBM and bf16 figures)"},
+        "e2e": {"value": e2e_val, "unit": "point-edge evals/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "note": "pinned H2D of points+poses, exact_sdf_batch, D2H of per-pose min+argmin; "
+                        "the full distance matrix stays in HBM"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if not args.no_extra:
+        line["extra"] = mppi_extra(torch, ex, dev)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extra", action="store_true", help="skip the MPPI cycle measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target length of the CPU oracle sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

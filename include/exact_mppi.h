@@ -1,0 +1,159 @@
+/*
+ * exact_mppi.h -- C ABI of the GB300 (sm_103a) EXACT-MPPI hot path.
+ *
+ * EXACT-MPPI (arXiv 2605.29663) scores K sampled control sequences over a
+ * horizon T by rolling them out through a kinematic model (Sec. III-D),
+ * moving all N obstacle points into every predicted body frame (Sec. IV-C.1)
+ * and taking each point's exact signed distance to the robot footprint
+ * (simple polygon: Sec. IV-C.3; rectangle cover: Sec. IV-C.2).  The per-step
+ * minima feed the collision / clearance cost and the unsafe flag (Sec. IV-E),
+ * and the cycle ends with the softmax-weighted update, the validation of the
+ * updated nominal and the shift or reset (Sec. III-E, Algorithm 1).
+ *
+ * Conventions for every entry point below:
+ *  - Array arguments marked "device" are caller-owned device memory of the
+ *    current CUDA device; the library never frees or retains them.  Arrays
+ *    are dense, row-major, float32 unless stated.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream; results are valid once
+ *    the stream has been synchronised.
+ *  - The return value reports argument and launch errors (exact_status).
+ *    Errors found on the device (exact_ctx_get_error) are reported later.
+ *  - No C++ exception crosses this boundary.  Thread-compatible: objects may
+ *    be used from several host threads only with external synchronisation.
+ */
+#ifndef EXACT_MPPI_H
+#define EXACT_MPPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EXACT_OK = 0,
+    EXACT_EINVAL = 1,       /* bad argument (NULL, negative size, non-finite value) */
+    EXACT_ENOTSIMPLE = 2,   /* polygon is not simple (self-intersection, repeated vertex, zero area) */
+    EXACT_ECAPACITY = 3,    /* size beyond a documented maximum */
+    EXACT_ECUDA = 4,        /* a CUDA runtime call failed */
+    EXACT_ETIMEOUT = 5      /* a bounded device-side wait gave up */
+} exact_status;
+
+typedef enum { EXACT_FP_POLYGON = 0, EXACT_FP_RECTS = 1 } exact_fp_kind;
+
+/* Motion models of Sec. III-D and their control vectors:
+ * DIFF (v, omega), ACKERMANN (v, delta), OMNI (vx, vy, omega),
+ * SPIN (omega), PARALLEL (v_para). */
+typedef enum {
+    EXACT_MM_DIFF = 0, EXACT_MM_ACKERMANN = 1, EXACT_MM_OMNI = 2,
+    EXACT_MM_SPIN = 3, EXACT_MM_PARALLEL = 4
+} exact_motion;
+
+#define EXACT_MAX_POLY_VERTICES 64
+#define EXACT_MAX_RECTS 8
+#define EXACT_MAX_HORIZON 128
+#define EXACT_MAX_SAMPLES 65536
+
+/* Human-readable name of an exact_status value (static string). */
+const char *exact_status_string(int status);
+
+/* ------------------------------------------------------------------ footprint
+ * Effective footprint B_eff (Sec. III-B, IV-B), fixed in the body frame.
+ * kind = EXACT_FP_POLYGON: host_data = n cyclic vertices (x, y), 3 <= n <= 64,
+ *   either orientation (Sec. IV-B.2).  Rejected with EXACT_ENOTSIMPLE when
+ *   the boundary self-intersects (O(n^2) host check), repeats a vertex or
+ *   encloses zero area.
+ * kind = EXACT_FP_RECTS: host_data = n boxes (cx, cy, sx, sy) with half
+ *   extents sx, sy > 0, 1 <= n <= 8 (Sec. IV-B.1).
+ * The library copies host_data; *out is owned by the caller and released
+ * with exact_footprint_destroy.  Changing the footprint means creating a new
+ * object: no recompilation and no device allocation is involved. */
+typedef struct exact_footprint exact_footprint;
+int exact_footprint_create(int kind, const float *host_data, int n, exact_footprint **out);
+void exact_footprint_destroy(exact_footprint *fp);
+/* Kind and number of vertices / boxes of a footprint. */
+int exact_footprint_info(const exact_footprint *fp, int *kind, int *n);
+
+/* ------------------------------------------------------------------ context
+ * A context owns the device scratch of mppi_step and of the multi-block
+ * exact_sdf_batch reduction, plus a device error word.  It is bound to the
+ * device that is current at creation.  Scratch grows on demand (a call with
+ * larger sizes than any before may allocate, which must not happen during
+ * stream capture); exact_ctx_reserve allocates ahead of time. */
+typedef struct exact_ctx exact_ctx;
+int exact_ctx_create(exact_ctx **out);
+void exact_ctx_destroy(exact_ctx *ctx);
+/* Make sure scratch for sdf batches of up to max_poses poses and MPPI steps
+ * of up to max_K samples and max_T steps exists (synchronous). */
+int exact_ctx_reserve(exact_ctx *ctx, int max_poses, int max_K, int max_T);
+/* Device-side error word (an exact_status); synchronises the device, then
+ * returns and clears it. */
+int exact_ctx_get_error(exact_ctx *ctx);
+
+/* ------------------------------------------------------------------ SDF batch
+ * Batched exact signed distance (Sec. IV-C, IV-D; the evaluator of
+ * Experiment 1).  For pose p = (x, y, theta) and point o_i every point is
+ * moved into the body frame, p_i = R(theta)^T (o_i - (x, y)), and its signed
+ * distance to the footprint is taken (negative inside).
+ *   points  device, n_points x 2 (x, y) in the planning frame
+ *   mask    device, n_points uint8 (0 = padding) or NULL (all valid)
+ *   poses   device, n_poses x 3 (x, y, theta)
+ *   dist    device, n_poses x n_points, or NULL: signed distances; padded
+ *           points get +inf
+ *   dmin    device, n_poses, or NULL: masked minimum (+inf if no valid point)
+ *   argmin  device, n_poses int32, or NULL: index of the minimum (lowest
+ *           index among equal float32 keys; -1 if no valid point)
+ * n_points, n_poses >= 0 (0 is a no-op); n_points * n_poses < 2^62.  ctx
+ * supplies scratch when many blocks share one pose; it may be NULL, in which
+ * case each pose is reduced by a single block. */
+int exact_sdf_batch(exact_ctx *ctx, const float *points, const uint8_t *mask, int n_points,
+                    const float *poses, int n_poses, const exact_footprint *fp,
+                    float *dist, float *dmin, int *argmin, void *stream);
+
+/* ------------------------------------------------------------------ MPPI step
+ * Parameters of one control cycle (Algorithm 1 "Params" plus the task /
+ * control cost of Sec. III-E, which the paper leaves open):
+ *   J = sum_h [ w_goal * dist(s_h, guidance) + w_ctrl * |u_h|^2 + phi_obs(d_h) ]
+ *       + w_term * dist(q_T, guidance),
+ *   phi_obs(d) = w_coll * I(d < 0) + w_rep * max(d_safe - d, 0)^2,
+ *   chi = OR_h (d_h < d_safe),  J~ = J + w_inf * I(chi),
+ * where s_h = q_{h+1} (state_offset = 1) or q_h (state_offset = 0, the
+ * printed indexing).  clamp != 0 clips every sampled control to
+ * [u_min, u_max] and uses the clipped perturbation in the update. */
+typedef struct {
+    int K, T, n_u, model;             /* samples, horizon, control dim, exact_motion */
+    float dt, lambda, d_safe;
+    float w_coll, w_rep, w_inf, w_goal, w_term, w_ctrl;
+    float wheelbase;                  /* Ackermann L */
+    float u_min[3], u_max[3];
+    int clamp, state_offset;
+} exact_mppi_params;
+
+/* One batched EXACT-MPPI control cycle (Algorithm 1) for one robot.
+ *   state     device, 3: q_0 = (x, y, theta)
+ *   cloud     device, n_points x 2 obstacle points; mask device n_points or NULL
+ *   waypoints device, n_wp x 2: a goal point (n_wp = 1) or a polyline
+ *   U         device, T x n_u, in/out: the nominal sequence; on return the
+ *             shifted sequence (last entry repeated) if validation passed,
+ *             all zeros otherwise
+ *   noise     device, K x T x n_u perturbations eps (Sec. III-E)
+ *   u_star    device, n_u: the executed command (zero on validation failure)
+ *   costs     device, K, or NULL: J~ per sample
+ *   weights   device, K, or NULL: omega per sample
+ *   valid     device, 1 int32, or NULL: 1 if the updated nominal passed
+ *   U_upd     device, T x n_u, or NULL: the updated nominal before shift/reset
+ *   dmin      device, K x T, or NULL: d_min of every scored rollout state
+ * Limits: 1 <= K <= 65536, 1 <= T <= 128, n_points >= 0, n_wp >= 1,
+ * n_u must match the model.  Scratch comes from ctx (grown on demand). */
+int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint8_t *mask,
+              int n_points, const float *waypoints, int n_wp, float *U, const float *noise,
+              const exact_footprint *fp, const exact_mppi_params *params,
+              float *u_star, float *costs, float *weights, int *valid, float *U_upd,
+              float *dmin, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXACT_MPPI_H */

@@ -1,0 +1,275 @@
+"""EXACT-MPPI hot path on GB300 (sm_103a): thin Python binding of the C ABI.
+
+Every step of the method runs in the CUDA library ``_lib/libexact_mppi.so``
+(declared in ``include/exact_mppi.h``).  This module only marshals
+arguments: it checks dtypes, devices and shapes of torch tensors, allocates
+outputs with torch (device memory is torch's job here) and passes raw
+pointers and the current CUDA stream through ctypes.  There is no CPU
+fallback: if the library has not been built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+__all__ = ["load", "Footprint", "Context", "MppiParams", "sdf_batch", "mppi_step", "ExactError",
+           "POLYGON", "RECTS", "DIFF", "ACKERMANN", "OMNI", "SPIN", "PARALLEL", "NU", "EXPORTS"]
+
+POLYGON, RECTS = 0, 1
+DIFF, ACKERMANN, OMNI, SPIN, PARALLEL = 0, 1, 2, 3, 4
+NU = {DIFF: 2, ACKERMANN: 2, OMNI: 3, SPIN: 1, PARALLEL: 1}
+
+# every symbol declared in include/exact_mppi.h
+EXPORTS = ["exact_status_string", "exact_footprint_create", "exact_footprint_destroy",
+           "exact_footprint_info", "exact_ctx_create", "exact_ctx_destroy", "exact_ctx_reserve",
+           "exact_ctx_get_error", "exact_sdf_batch", "mppi_step"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ExactError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+def load() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB_PATH):
+            raise RuntimeError(f"{_build.LIB_PATH} is missing: build it with "
+                               "`python -m paper_2605_29663_gb300.build` (nvcc, sm_103a)")
+        lib = ctypes.CDLL(_build.LIB_PATH)
+        P, I, V = ctypes.c_void_p, ctypes.c_int, None
+        lib.exact_status_string.restype = ctypes.c_char_p
+        lib.exact_status_string.argtypes = [I]
+        lib.exact_footprint_create.restype = I
+        lib.exact_footprint_create.argtypes = [I, P, I, ctypes.POINTER(P)]
+        lib.exact_footprint_destroy.restype = V
+        lib.exact_footprint_destroy.argtypes = [P]
+        lib.exact_footprint_info.restype = I
+        lib.exact_footprint_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+        lib.exact_ctx_create.restype = I
+        lib.exact_ctx_create.argtypes = [ctypes.POINTER(P)]
+        lib.exact_ctx_destroy.restype = V
+        lib.exact_ctx_destroy.argtypes = [P]
+        lib.exact_ctx_reserve.restype = I
+        lib.exact_ctx_reserve.argtypes = [P, I, I, I]
+        lib.exact_ctx_get_error.restype = I
+        lib.exact_ctx_get_error.argtypes = [P]
+        lib.exact_sdf_batch.restype = I
+        lib.exact_sdf_batch.argtypes = [P, P, P, I, P, I, P, P, P, P, P]
+        lib.mppi_step.restype = I
+        lib.mppi_step.argtypes = [P, P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    return load().exact_status_string(int(status)).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise ExactError(rc, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(t, name, dtype=None, shape=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+def _stream(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Footprint:
+    """Effective footprint (Sec. III-B): a simple polygon (n x 2 vertices) or a
+    rectangle cover (n x 4: cx, cy, sx, sy)."""
+
+    def __init__(self, kind: int, data):
+        import numpy as np
+        arr = np.ascontiguousarray(np.asarray(data, dtype=np.float32))
+        per = 2 if kind == POLYGON else 4
+        arr = arr.reshape(-1, per)
+        h = ctypes.c_void_p()
+        _check(load().exact_footprint_create(kind, arr.ctypes.data, arr.shape[0], ctypes.byref(h)),
+               "exact_footprint_create")
+        self._h = h
+        self.kind = kind
+        self.n = arr.shape[0]
+        self.data = arr.copy()
+
+    @classmethod
+    def polygon(cls, verts):
+        return cls(POLYGON, verts)
+
+    @classmethod
+    def rects(cls, boxes):
+        return cls(RECTS, boxes)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().exact_footprint_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """Device scratch arena + error word (bound to the current device)."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(load().exact_ctx_create(ctypes.byref(h)), "exact_ctx_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reserve(self, max_poses: int = 0, max_K: int = 0, max_T: int = 0):
+        _check(load().exact_ctx_reserve(self._h, max_poses, max_K, max_T), "exact_ctx_reserve")
+
+    def get_error(self) -> int:
+        return load().exact_ctx_get_error(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().exact_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sdf_batch(points, poses, footprint: Footprint, mask=None, *, dist=True, dmin=True, argmin=True,
+              ctx: Context | None = None, out=None, stream=None):
+    """Batched body-frame signed distances (Sec. IV-C/D).  Returns
+    (dist [P, N] | None, dmin [P] | None, argmin [P] int32 | None)."""
+    torch = _torch()
+    points = _dev(points, "points", torch.float32)
+    poses = _dev(poses, "poses", torch.float32)
+    N = points.shape[0] if points.numel() else 0
+    P = poses.shape[0]
+    if points.numel() and (points.dim() != 2 or points.shape[1] != 2):
+        raise ValueError("points must be N x 2")
+    if poses.dim() != 2 or poses.shape[1] != 3:
+        raise ValueError("poses must be P x 3")
+    if mask is not None:
+        mask = _dev(mask, "mask", torch.uint8, (N,))
+    o = out or {}
+    d = o.get("dist") if dist else None
+    if dist and d is None:
+        d = torch.empty((P, N), dtype=torch.float32, device=poses.device)
+    m = o.get("dmin") if dmin else None
+    if dmin and m is None:
+        m = torch.empty(P, dtype=torch.float32, device=poses.device)
+    a = o.get("argmin") if argmin else None
+    if argmin and a is None:
+        a = torch.empty(P, dtype=torch.int32, device=poses.device)
+    _check(load().exact_sdf_batch(ctx.handle if ctx else None, _ptr(points) if N else None, _ptr(mask), N,
+                                  _ptr(poses), P, footprint.handle, _ptr(d), _ptr(m), _ptr(a),
+                                  _stream(stream)), "exact_sdf_batch")
+    return d, m, a
+
+
+class MppiParams(ctypes.Structure):
+    """Mirror of exact_mppi_params."""
+    _fields_ = [("K", ctypes.c_int), ("T", ctypes.c_int), ("n_u", ctypes.c_int), ("model", ctypes.c_int),
+                ("dt", ctypes.c_float), ("lam", ctypes.c_float), ("d_safe", ctypes.c_float),
+                ("w_coll", ctypes.c_float), ("w_rep", ctypes.c_float), ("w_inf", ctypes.c_float),
+                ("w_goal", ctypes.c_float), ("w_term", ctypes.c_float), ("w_ctrl", ctypes.c_float),
+                ("wheelbase", ctypes.c_float),
+                ("u_min", ctypes.c_float * 3), ("u_max", ctypes.c_float * 3),
+                ("clamp", ctypes.c_int), ("state_offset", ctypes.c_int)]
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "MppiParams":
+        p = cls()
+        p.K, p.T, p.n_u, p.model = int(d["K"]), int(d["T"]), int(d["nu"]), int(d["model"])
+        for k in ("dt", "d_safe", "w_coll", "w_rep", "w_inf", "w_goal", "w_term", "w_ctrl", "wheelbase"):
+            setattr(p, k, float(d[k]))
+        p.lam = float(d["lambda"])
+        for j in range(3):
+            p.u_min[j] = max(float(d["u_min"][j]), -3.0e38)
+            p.u_max[j] = min(float(d["u_max"][j]), 3.0e38)
+        p.clamp = int(d["clamp"])
+        p.state_offset = int(d["state_offset"])
+        return p
+
+
+def mppi_step(ctx: Context, state, cloud, waypoints, U, noise, footprint: Footprint, params, mask=None, *,
+              costs=True, weights=True, U_upd=True, dmin=False, out=None, stream=None) -> dict:
+    """One EXACT-MPPI control cycle (Algorithm 1).  U is updated in place
+    (shifted, or reset to zero when validation fails).  Returns a dict of
+    device tensors: u_star, valid, and the requested costs / weights /
+    U_upd / dmin."""
+    torch = _torch()
+    p = params if isinstance(params, MppiParams) else MppiParams.from_dict(params)
+    K, T, nu = p.K, p.T, p.n_u
+    state = _dev(state, "state", torch.float32, (3,))
+    U = _dev(U, "U", torch.float32, (T, nu))
+    noise = _dev(noise, "noise", torch.float32, (K, T, nu))
+    waypoints = _dev(waypoints, "waypoints", torch.float32)
+    W = waypoints.shape[0]
+    cloud = _dev(cloud, "cloud", torch.float32)
+    N = cloud.shape[0] if cloud.numel() else 0
+    if mask is not None:
+        mask = _dev(mask, "mask", torch.uint8, (N,))
+    dev = U.device
+    o = dict(out or {})
+    if "u_star" not in o:
+        o["u_star"] = torch.empty(nu, dtype=torch.float32, device=dev)
+    if "valid" not in o:
+        o["valid"] = torch.empty(1, dtype=torch.int32, device=dev)
+    if costs and "costs" not in o:
+        o["costs"] = torch.empty(K, dtype=torch.float32, device=dev)
+    if weights and "weights" not in o:
+        o["weights"] = torch.empty(K, dtype=torch.float32, device=dev)
+    if U_upd and "U_upd" not in o:
+        o["U_upd"] = torch.empty((T, nu), dtype=torch.float32, device=dev)
+    if dmin and "dmin" not in o:
+        o["dmin"] = torch.empty((K, T), dtype=torch.float32, device=dev)
+    _check(load().mppi_step(ctx.handle, _ptr(state), _ptr(cloud) if N else None, _ptr(mask), N,
+                            _ptr(waypoints), W, _ptr(U), _ptr(noise), footprint.handle, ctypes.byref(p),
+                            _ptr(o["u_star"]), _ptr(o.get("costs")), _ptr(o.get("weights")), _ptr(o["valid"]),
+                            _ptr(o.get("U_upd")), _ptr(o.get("dmin")), _stream(stream)), "mppi_step")
+    return o

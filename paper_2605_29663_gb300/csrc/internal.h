@@ -1,0 +1,93 @@
+// internal.h -- host-side objects and dispatch shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "exact_mppi.h"
+
+struct exact_footprint {
+    int kind;    // exact_fp_kind
+    int n;       // vertices or boxes given by the caller
+    int n_pad;   // evaluator size the constants are padded to
+    // polygon: per-edge constants (see exact::PolyC); rects: boxes
+    float vx[EXACT_MAX_POLY_VERTICES], vy[EXACT_MAX_POLY_VERTICES];
+    float exn[EXACT_MAX_POLY_VERTICES], eyn[EXACT_MAX_POLY_VERTICES];
+    float ex[EXACT_MAX_POLY_VERTICES], ey[EXACT_MAX_POLY_VERTICES];
+    float kx[EXACT_MAX_POLY_VERTICES];
+    float cx[EXACT_MAX_RECTS], cy[EXACT_MAX_RECTS], sx[EXACT_MAX_RECTS], sy[EXACT_MAX_RECTS];
+};
+
+struct exact_ctx {
+    int device = 0;
+    int sm_count = 0;
+    void *scratch = nullptr;     // growable device arena
+    size_t scratch_bytes = 0;
+    int *d_err = nullptr;        // device error word (exact_status)
+};
+
+namespace exact {
+
+// Grow the context arena to at least `bytes` (synchronous when it grows).
+int ensure_scratch(exact_ctx *ctx, size_t bytes);
+int current_sm_count();
+// Arena bytes needed by exact_sdf_batch (n_poses) and mppi_step (K, T).
+size_t sdf_scratch_bytes(int n_poses);
+size_t mppi_scratch_bytes(int K, int T);
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <int E>
+inline PolyC<E> make_poly(const exact_footprint *fp) {
+    PolyC<E> P;
+    for (int b = 0; b < E; ++b) {
+        P.vx[b] = fp->vx[b]; P.vy[b] = fp->vy[b];
+        P.exn[b] = fp->exn[b]; P.eyn[b] = fp->eyn[b];
+        P.ex[b] = fp->ex[b]; P.ey[b] = fp->ey[b];
+        P.kx[b] = fp->kx[b];
+    }
+    return P;
+}
+
+template <int R>
+inline RectC<R> make_rect(const exact_footprint *fp) {
+    RectC<R> Q;
+    for (int j = 0; j < R; ++j) {
+        Q.cx[j] = fp->cx[j]; Q.cy[j] = fp->cy[j]; Q.sx[j] = fp->sx[j]; Q.sy[j] = fp->sy[j];
+    }
+    return Q;
+}
+
+// Calls f(constants) with the footprint's constant block of its padded size.
+template <class F>
+int with_footprint(const exact_footprint *fp, F &&f) {
+    if (fp->kind == EXACT_FP_POLYGON) {
+        switch (fp->n_pad) {
+        case 4: return f(make_poly<4>(fp));
+        case 8: return f(make_poly<8>(fp));
+        case 12: return f(make_poly<12>(fp));
+        case 16: return f(make_poly<16>(fp));
+        case 24: return f(make_poly<24>(fp));
+        case 32: return f(make_poly<32>(fp));
+        case 40: return f(make_poly<40>(fp));
+        case 48: return f(make_poly<48>(fp));
+        case 56: return f(make_poly<56>(fp));
+        case 64: return f(make_poly<64>(fp));
+        default: return EXACT_EINVAL;
+        }
+    }
+    switch (fp->n_pad) {
+    case 1: return f(make_rect<1>(fp));
+    case 2: return f(make_rect<2>(fp));
+    case 4: return f(make_rect<4>(fp));
+    case 8: return f(make_rect<8>(fp));
+    default: return EXACT_EINVAL;
+    }
+}
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? EXACT_OK : EXACT_ECUDA; }
+
+}  // namespace exact

@@ -1,0 +1,366 @@
+// mppi.cu -- mppi_step: one batched EXACT-MPPI control cycle (Algorithm 1).
+//
+// Three kernels, stream-ordered (and capturable in one CUDA graph):
+//   A  mppi_sample_kernel   one block per sample r: warp-parallel rollout,
+//                           then every (step, point) body-frame signed
+//                           distance with per-step minima in shared memory,
+//                           then phi_task + phi_ctrl + phi_obs, chi and J.
+//   B1 mppi_update_kernel   one block: beta = min J~, the softmax weights, U += sum_r omega_r eps_r, and the
+//                           rollout of the updated nominal.
+//   B2 mppi_validate_kernel one block per (step, point chunk) of the nominal:
+//                           d_min >= d_safe; the last block to finish (atomic
+//                           ticket, no waiting) writes u*, the shifted or
+//                           reset U and the valid flag.
+// No K x T x N intermediate touches memory; the only scratch is per-sample
+// J / chi and per-step nominal data in the context arena.
+#include "internal.h"
+#include "mppi_common.cuh"
+
+namespace exact {
+
+struct MppiScratch {
+    double *J;          // K
+    int *chi;           // K
+    float *wt;          // K   unnormalised weights exp(-(J~ - beta)/lambda)
+    float *U_upd;       // T x nu
+    float4 *nom_pose;   // T   scored nominal states (x, y, cos, sin)
+    int *bad;           // 1   validation failed
+    unsigned *ticket;   // 1   finished validation blocks
+};
+
+size_t mppi_scratch_bytes(int K, int T) {
+    size_t b = 0;
+    b += align_up((size_t)K * sizeof(double), 256);
+    b += align_up((size_t)K * sizeof(int), 256);
+    b += align_up((size_t)K * sizeof(float), 256);
+    b += align_up((size_t)T * 3 * sizeof(float), 256);
+    b += align_up((size_t)T * sizeof(float4), 256);
+    b += 256 + 256;
+    return b;
+}
+
+static MppiScratch carve(void *base, int K, int T) {
+    char *p = static_cast<char *>(base);
+    MppiScratch s;
+    s.J = reinterpret_cast<double *>(p); p += align_up((size_t)K * sizeof(double), 256);
+    s.chi = reinterpret_cast<int *>(p); p += align_up((size_t)K * sizeof(int), 256);
+    s.wt = reinterpret_cast<float *>(p); p += align_up((size_t)K * sizeof(float), 256);
+    s.U_upd = reinterpret_cast<float *>(p); p += align_up((size_t)T * 3 * sizeof(float), 256);
+    s.nom_pose = reinterpret_cast<float4 *>(p); p += align_up((size_t)T * sizeof(float4), 256);
+    s.bad = reinterpret_cast<int *>(p); p += 256;
+    s.ticket = reinterpret_cast<unsigned *>(p);
+    return s;
+}
+
+// Per-step minimum over all points of the body-frame key, for the poses in
+// shared memory; each block thread walks point pairs, warps meet in
+// shared-memory atomics on order-preserving keys.
+template <class FPC>
+__device__ __forceinline__ void steps_min_keys(const FPC &fpc, const float2 *__restrict__ pts,
+                                               const uint8_t *__restrict__ mask, int N, const float4 *pose,
+                                               int T, unsigned *keyh) {
+    const int npairs = (N + 1) >> 1;
+    for (int h = 0; h < T; ++h) {
+        const float4 q = pose[h];
+        float best = finf();
+        for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
+            const int i0 = 2 * j, i1 = 2 * j + 1;
+            const bool has1 = i1 < N;
+            const float2 o0 = __ldg(pts + i0);
+            const float2 o1 = has1 ? __ldg(pts + i1) : o0;
+            float px0, py0, px1, py1;
+            body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
+            body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
+            float k0, k1;
+            eval2(fpc, px0, py0, px1, py1, k0, k1);
+            const bool v0 = mask ? __ldg(mask + i0) != 0 : true;
+            const bool v1 = has1 && (mask ? __ldg(mask + i1) != 0 : true);
+            if (v0) best = fminf(best, k0);   // fminf ignores a NaN key
+            if (v1) best = fminf(best, k1);
+        }
+        best = warp_min_f(best);
+        if ((threadIdx.x & 31) == 0) atomicMin(keyh + h, f2ord(best));
+    }
+}
+
+template <class FPC>
+__global__ void __launch_bounds__(kBlock)
+mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state,
+                   const float2 *__restrict__ pts, const uint8_t *__restrict__ mask, int N,
+                   const float *__restrict__ wp, int W, const float *__restrict__ U,
+                   const float *__restrict__ noise, double *__restrict__ Jout, int *__restrict__ chi_out,
+                   float *__restrict__ dmin_out) {
+    __shared__ float4 s_pose[EXACT_MAX_HORIZON];
+    __shared__ float s_stage[EXACT_MAX_HORIZON];
+    __shared__ unsigned s_key[EXACT_MAX_HORIZON];
+    __shared__ float s_term;
+    const int r = blockIdx.x;
+    const int T = P.T, nu = P.nu;
+    for (int h = threadIdx.x; h < T; h += blockDim.x) s_key[h] = f2ord(finf());
+
+    if (threadIdx.x < 32) {
+        const float *eps = noise + (size_t)r * T * nu;
+        LaneRollout R;
+        warp_rollout(P, state[0], state[1], state[2],
+                     [&](int h, int j) { return clamp_u(P, j, U[h * nu + j] + eps[h * nu + j]); }, R);
+        const int lane = threadIdx.x;
+#pragma unroll
+        for (int e = 0; e < kMaxPerLane; ++e) {
+            const int h = lane * R.per + e;
+            if (e < R.per && h < T) {
+                float sn, cs;
+                sincosf(R.th[e], &sn, &cs);
+                s_pose[h] = make_float4(R.x[e], R.y[e], cs, sn);
+                const float u2 = fmaf(R.u[e][0], R.u[e][0], fmaf(R.u[e][1], R.u[e][1], R.u[e][2] * R.u[e][2]));
+                s_stage[h] = fmaf(P.w_goal, guidance_dist(R.x[e], R.y[e], wp, W), P.w_ctrl * u2);
+            }
+        }
+        if (lane == 0) s_term = P.w_term * guidance_dist(R.qTx, R.qTy, wp, W);
+    }
+    __syncthreads();
+    steps_min_keys(fpc, pts, mask, N, s_pose, T, s_key);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double acc = 0.0;
+        bool unsafe = false;
+        for (int h = threadIdx.x; h < T; h += 32) {
+            const unsigned k = s_key[h];
+            const float key = ord2f(k);
+            const float d = key == finf() ? finf() : key_to_dist(fpc, key);
+            if (dmin_out) dmin_out[(size_t)r * T + h] = d;
+            acc += (double)s_stage[h] + (double)phi_obs(P, d);
+            unsafe |= d < P.d_safe;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const bool chi = __any_sync(0xffffffffu, unsafe);
+        if (threadIdx.x == 0) {
+            Jout[r] = acc + (double)s_term;
+            chi_out[r] = chi ? 1 : 0;
+        }
+    }
+}
+
+constexpr int kUpdBlock = 1024;
+
+// B1: weights, update and nominal rollout (one block).
+__global__ void __launch_bounds__(kUpdBlock)
+mppi_update_kernel(const MppiP P, const float *__restrict__ state, const float *__restrict__ U,
+                   const float *__restrict__ noise, MppiScratch S, float *__restrict__ costs,
+                   float *__restrict__ weights, float *__restrict__ U_upd_out) {
+    __shared__ double s_J[32];
+    __shared__ float s_f[32];
+    __shared__ float s_part[kUpdBlock];
+    __shared__ float s_U[EXACT_MAX_HORIZON * 3];
+    const int K = P.K, T = P.T, nu = P.nu, TN = T * nu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // beta = min_r J~_r, with J~ = J + w_inf I(chi) formed in double so that
+    // J~ - beta keeps the precision of J despite the large w_inf offset
+    double bJ = __longlong_as_double(0x7ff0000000000000ll);
+    for (int r = tid; r < K; r += kUpdBlock) bJ = fmin(bJ, S.J[r] + (double)P.w_inf * (double)S.chi[r]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bJ = fmin(bJ, __shfl_xor_sync(0xffffffffu, bJ, o));
+    if (lane == 0) s_J[warp] = bJ;
+    __syncthreads();
+    if (warp == 0) {
+        bJ = s_J[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bJ = fmin(bJ, __shfl_xor_sync(0xffffffffu, bJ, o));
+        if (lane == 0) s_J[0] = bJ;
+    }
+    __syncthreads();
+    const double beta = s_J[0];
+
+    // unnormalised weights and their sum Z
+    float z = 0.f;
+    for (int r = tid; r < K; r += kUpdBlock) {
+        const double diff = (S.J[r] + (double)P.w_inf * (double)S.chi[r]) - beta;
+        const float w = expf(-(float)diff / P.lambda);
+        S.wt[r] = w;
+        z += w;
+    }
+    z = warp_sum_f(z);
+    if (lane == 0) s_f[warp] = z;
+    __syncthreads();
+    if (warp == 0) {
+        z = warp_sum_f(s_f[lane]);
+        if (lane == 0) s_f[0] = z;
+    }
+    __syncthreads();
+    const float Z = s_f[0];
+    const float invZ = 1.f / Z;
+    if (weights || costs) {
+        for (int r = tid; r < K; r += kUpdBlock) {
+            if (weights) weights[r] = S.wt[r] * invZ;
+            if (costs) costs[r] = (float)(S.J[r] + (double)P.w_inf * (double)S.chi[r]);
+        }
+    }
+
+    // U_h += sum_r omega_r eps'_{r,h}: thread -> (element e, sample slice)
+    const int slices = kUpdBlock / TN;
+    const int e = tid % TN, sl = tid / TN;
+    float acc = 0.f;
+    if (sl < slices) {
+        const float ue = U[e];
+        const int j = e % nu;
+        for (int r = sl; r < K; r += slices) {
+            const float eps = noise[(size_t)r * TN + e];
+            const float ep = P.clamp ? clamp_u(P, j, ue + eps) - ue : eps;
+            acc = fmaf(S.wt[r], ep, acc);
+        }
+    }
+    s_part[tid] = acc;
+    __syncthreads();
+    if (tid < TN) {
+        float tot = 0.f;
+        for (int q = 0; q < slices; ++q) tot += s_part[q * TN + tid];
+        const float v = U[tid] + tot * invZ;
+        s_U[tid] = v;
+        S.U_upd[tid] = v;
+        if (U_upd_out) U_upd_out[tid] = v;
+    }
+    __syncthreads();
+
+    // rollout of the updated nominal (clamped like every sampled sequence)
+    if (warp == 0) {
+        LaneRollout R;
+        warp_rollout(P, state[0], state[1], state[2], [&](int h, int j) { return clamp_u(P, j, s_U[h * nu + j]); }, R);
+#pragma unroll
+        for (int q = 0; q < kMaxPerLane; ++q) {
+            const int h = lane * R.per + q;
+            if (q < R.per && h < T) {
+                float sn, cs;
+                sincosf(R.th[q], &sn, &cs);
+                S.nom_pose[h] = make_float4(R.x[q], R.y[q], cs, sn);
+            }
+        }
+        if (lane == 0) {
+            *S.bad = 0;
+            *S.ticket = 0u;
+        }
+    }
+}
+
+// B2: validation of the updated nominal and the final shift / reset.
+template <class FPC>
+__global__ void __launch_bounds__(kBlock)
+mppi_validate_kernel(const MppiP P, const FPC fpc, const float2 *__restrict__ pts,
+                     const uint8_t *__restrict__ mask, int N, int chunks, int chunk_pairs, MppiScratch S,
+                     float *__restrict__ U, float *__restrict__ u_star, int *__restrict__ valid_out) {
+    __shared__ float s_min[kBlock / 32];
+    __shared__ bool s_last;
+    const int h = blockIdx.x / chunks, chunk = blockIdx.x - h * chunks;
+    const float4 q = S.nom_pose[h];
+    const int npairs = (N + 1) >> 1;
+    const int pend = min(npairs, (chunk + 1) * chunk_pairs);
+    float best = finf();
+    for (int j = chunk * chunk_pairs + threadIdx.x; j < pend; j += kBlock) {
+        const int i0 = 2 * j, i1 = 2 * j + 1;
+        const bool has1 = i1 < N;
+        const float2 o0 = __ldg(pts + i0);
+        const float2 o1 = has1 ? __ldg(pts + i1) : o0;
+        float px0, py0, px1, py1;
+        body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
+        body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
+        float k0, k1;
+        eval2(fpc, px0, py0, px1, py1, k0, k1);
+        const bool v0 = mask ? __ldg(mask + i0) != 0 : true;
+        const bool v1 = has1 && (mask ? __ldg(mask + i1) != 0 : true);
+        // a NaN key fails validation (d >= d_safe is false)
+        if (v0) best = (k0 == k0) ? fminf(best, k0) : -finf();
+        if (v1) best = (k1 == k1) ? fminf(best, k1) : -finf();
+    }
+    best = warp_min_f(best);
+    if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = s_min[0];
+        for (int w = 1; w < kBlock / 32; ++w) b = fminf(b, s_min[w]);
+        const float d = b == finf() ? finf() : key_to_dist(fpc, b);
+        if (!(d >= P.d_safe)) atomicExch(S.bad, 1);
+        __threadfence();
+        const unsigned t = atomicAdd(S.ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int ok = atomicAdd(S.bad, 0) == 0;
+    const int T = P.T, nu = P.nu, TN = T * nu;
+    for (int e = threadIdx.x; e < TN; e += kBlock) {
+        const float v = S.U_upd[e];
+        if (e < nu && u_star) u_star[e] = ok ? v : 0.f;
+        // shift forward, repeating the last entry; or reset to zero
+        U[e] = ok ? (e + nu < TN ? S.U_upd[e + nu] : v) : 0.f;
+    }
+    if (threadIdx.x == 0) {
+        if (valid_out) *valid_out = ok;
+        *S.ticket = 0u;
+    }
+}
+
+}  // namespace exact
+
+using namespace exact;
+
+static int check_params(const exact_mppi_params *p) {
+    if (!p) return EXACT_EINVAL;
+    if (p->K < 1 || p->T < 1) return EXACT_EINVAL;
+    if (p->K > EXACT_MAX_SAMPLES || p->T > EXACT_MAX_HORIZON) return EXACT_ECAPACITY;
+    const int want = p->model == EXACT_MM_DIFF || p->model == EXACT_MM_ACKERMANN ? 2
+                   : p->model == EXACT_MM_OMNI ? 3
+                   : p->model == EXACT_MM_SPIN || p->model == EXACT_MM_PARALLEL ? 1 : -1;
+    if (want < 0 || p->n_u != want) return EXACT_EINVAL;
+    if (!(p->lambda > 0.f) || !(p->dt > 0.f) || !isfinite(p->lambda) || !isfinite(p->dt)) return EXACT_EINVAL;
+    if (p->model == EXACT_MM_ACKERMANN && !(p->wheelbase > 0.f)) return EXACT_EINVAL;
+    return EXACT_OK;
+}
+
+static MppiP to_device_params(const exact_mppi_params *p) {
+    MppiP d;
+    d.K = p->K; d.T = p->T; d.nu = p->n_u; d.model = p->model;
+    d.dt = p->dt; d.lambda = p->lambda; d.d_safe = p->d_safe;
+    d.w_coll = p->w_coll; d.w_rep = p->w_rep; d.w_inf = p->w_inf;
+    d.w_goal = p->w_goal; d.w_term = p->w_term; d.w_ctrl = p->w_ctrl; d.wheelbase = p->wheelbase;
+    for (int j = 0; j < 3; ++j) { d.u_min[j] = p->u_min[j]; d.u_max[j] = p->u_max[j]; }
+    d.clamp = p->clamp; d.state_offset = p->state_offset ? 1 : 0;
+    return d;
+}
+
+extern "C" int exact_ctx_reserve(exact_ctx *ctx, int max_poses, int max_K, int max_T) {
+    if (!ctx || max_poses < 0 || max_K < 0 || max_T < 0) return EXACT_EINVAL;
+    size_t need = sdf_scratch_bytes(max_poses);
+    const size_t m = mppi_scratch_bytes(max_K, max_T);
+    if (m > need) need = m;
+    return ensure_scratch(ctx, need);
+}
+
+extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint8_t *mask,
+                         int n_points, const float *waypoints, int n_wp, float *U, const float *noise,
+                         const exact_footprint *fp, const exact_mppi_params *params,
+                         float *u_star, float *costs, float *weights, int *valid, float *U_upd,
+                         float *dmin, void *stream) {
+    if (!ctx || !fp || !state || !U || !noise || !waypoints || n_wp < 1 || n_points < 0) return EXACT_EINVAL;
+    if (n_points > 0 && (!cloud || ((uintptr_t)cloud & 7u) != 0)) return EXACT_EINVAL;
+    int rc = check_params(params);
+    if (rc != EXACT_OK) return rc;
+    const MppiP P = to_device_params(params);
+    rc = ensure_scratch(ctx, mppi_scratch_bytes(P.K, P.T));
+    if (rc != EXACT_OK) return rc;
+    const MppiScratch S = carve(ctx->scratch, P.K, P.T);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float2 *pts = reinterpret_cast<const float2 *>(cloud);
+    const int npairs = (n_points + 1) / 2;
+    const int chunk_pairs = 1024;
+    const int chunks = npairs > chunk_pairs ? (npairs + chunk_pairs - 1) / chunk_pairs : 1;
+    return with_footprint(fp, [&](auto fpc) -> int {
+        using FPC = decltype(fpc);
+        mppi_sample_kernel<FPC><<<P.K, kBlock, 0, st>>>(P, fpc, state, pts, mask, n_points, waypoints, n_wp, U,
+                                                        noise, S.J, S.chi, dmin);
+        mppi_update_kernel<<<1, kUpdBlock, 0, st>>>(P, state, U, noise, S, costs, weights, U_upd);
+        mppi_validate_kernel<FPC><<<P.T * chunks, kBlock, 0, st>>>(P, fpc, pts, mask, n_points, chunks,
+                                                                   chunk_pairs, S, U, u_star, valid);
+        return cuda_status(cudaGetLastError());
+    });
+}

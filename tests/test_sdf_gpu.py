@@ -1,0 +1,211 @@
+"""Parity of exact_sdf_batch (CUDA, through the C ABI) with the FP64 oracle.
+
+Tolerances (from the signed-distance requirement): |d_gpu - d_oracle| <= 2e-5 m
+for coordinates up to 20 m; inside/outside flags bit-exact except within
+1e-5 m of the boundary; the per-pose minimum equals the minimum of the GPU's
+own row bit-exactly (same float32 key); the argmin is valid (its oracle
+distance is the oracle minimum within 2 * 2e-5)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+BAND = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ex():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_29663_gb300 import build
+    build.build()
+    import paper_2605_29663_gb300 as ex
+    return ex
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_gpu(ex, pts, poses, kind, fp, mask=None, ctx=None, dist=True):
+    import torch
+    f = ex.Footprint(kind, fp)
+    d, m, a = ex.sdf_batch(_t(pts.astype(np.float32)), _t(poses.astype(np.float32)), f,
+                           mask=None if mask is None else _t(mask), ctx=ctx, dist=dist)
+    torch.cuda.synchronize()
+    return (None if d is None else d.cpu().numpy()), m.cpu().numpy(), a.cpu().numpy()
+
+
+def check(pts, poses, kind, fp, dg, mg, ag, mask=None, rows=None):
+    rows = np.arange(poses.shape[0]) if rows is None else rows
+    do, mo, ao = oracle.sdf_batch(pts, poses[rows], kind, fp, mask=mask)
+    if dg is not None:
+        dgr = dg[rows]
+        assert np.array_equal(np.isinf(dgr), np.isinf(do))
+        fin = np.isfinite(do)
+        if fin.any():
+            err = np.abs(dgr[fin] - do[fin])
+            assert err.max() <= TOL, f"max abs err {err.max():.3g}"
+            band = fin & (np.abs(do) >= BAND)
+            assert np.array_equal(dgr[band] < 0, do[band] < 0), "inside flags differ"
+        # the minimum is the GPU row's own minimum, bit for bit
+        np.testing.assert_array_equal(mg[rows], np.min(dgr, axis=1) if dgr.shape[1] else np.full(len(rows), np.inf))
+    mgr = mg[rows]
+    assert np.array_equal(np.isinf(mgr), np.isinf(mo))
+    fin = np.isfinite(mo)
+    assert np.all(np.abs(mgr[fin] - mo[fin]) <= TOL)
+    agr = ag[rows]
+    assert np.all(agr[~fin] == -1)
+    if fin.any():
+        idx = np.nonzero(fin)[0]
+        d_at = oracle.sdf_batch(pts, poses[rows][idx], kind, fp, mask=mask)[0][np.arange(idx.size), agr[idx]]
+        assert np.all(np.abs(d_at - mo[idx]) <= 2 * TOL)
+
+
+def _poses(g, P, half=5.0):
+    p = np.empty((P, 3), np.float32)
+    p[:, :2] = g.uniform(-half, half, (P, 2))
+    p[:, 2] = g.uniform(-math.pi, math.pi, P)
+    return p
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6, 8, 9, 12, 13, 16, 17, 24, 31, 32, 33, 40, 47, 48, 56, 63, 64])
+def test_polygon_every_bucket(ex, n):
+    g = np.random.default_rng(100 + n)
+    fp = synth.star_polygon(g, n, 0.3, 1.2)
+    pts = synth.uniform_points(g, 1001, -3.0, 3.0)      # odd: ragged last pair
+    poses = _poses(g, 37, 2.0)
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.POLYGON, fp)
+    check(pts, poses, synth.POLYGON, fp, dg, mg, ag)
+
+
+@pytest.mark.parametrize("which", ["l", "l_gap", "l_cw"])
+def test_concave_l_shapes(ex, which):
+    fp = {"l": synth.l_footprint(), "l_gap": synth.l_footprint_gap(),
+          "l_cw": synth.l_footprint()[::-1].copy()}[which]
+    g = np.random.default_rng(7)
+    pts = synth.uniform_points(g, 2048, -3.0, 3.0)
+    poses = _poses(g, 64, 1.5)
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.POLYGON, fp)
+    check(pts, poses, synth.POLYGON, fp, dg, mg, ag)
+
+
+@pytest.mark.parametrize("rects", [synth.forklift_rects(), np.array([[0.2, -0.1, 0.5, 0.3]], np.float32),
+                                   np.array([[0, 0.5, 1, 0.2], [0, -0.2, 0.25, 0.6]], np.float32),
+                                   np.array([[i * 0.3, 0.1 * i, 0.2, 0.1 + 0.05 * i] for i in range(5)], np.float32),
+                                   np.array([[i * 0.2 - 0.8, 0.0, 0.15, 0.4] for i in range(8)], np.float32)])
+def test_rect_cover(ex, rects):
+    g = np.random.default_rng(int(rects.size))
+    pts = synth.uniform_points(g, 3001, -4.0, 4.0)
+    poses = _poses(g, 41, 2.0)
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.RECTS, rects)
+    check(pts, poses, synth.RECTS, rects, dg, mg, ag)
+
+
+def test_microbench_shape_small(ex):
+    w = synth.sdf_microbench(seed=3, n_poses=256, n_points=4097, n_vertices=32)
+    dg, mg, ag = run_gpu(ex, w["points"], w["poses"], w["kind"], w["fp"])
+    check(w["points"], w["poses"], w["kind"], w["fp"], dg, mg, ag)
+
+
+def test_far_coordinates_20m(ex):
+    g = np.random.default_rng(11)
+    pts = synth.uniform_points(g, 2000, -10.0, 10.0)
+    poses = _poses(g, 32, 10.0)                          # |o - t| up to ~28 m, coords <= 20 m
+    fp = synth.star_polygon(g, 24, 0.3, 1.2)
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.POLYGON, fp)
+    check(pts, poses, synth.POLYGON, fp, dg, mg, ag)
+
+
+def test_special_headings(ex):
+    g = np.random.default_rng(12)
+    pts = synth.uniform_points(g, 999, -2.0, 2.0)
+    poses = np.array([[0, 0, 0], [0.1, -0.2, math.pi / 2], [0, 0, math.pi], [0.3, 0.3, -math.pi],
+                      [0, 0, -math.pi / 2]], np.float32)
+    for kind, fp in ((synth.POLYGON, synth.l_footprint()), (synth.RECTS, synth.forklift_rects())):
+        dg, mg, ag = run_gpu(ex, pts, poses, kind, fp)
+        check(pts, poses, kind, fp, dg, mg, ag)
+
+
+def test_points_on_vertex_heights(ex):
+    # query points sharing vertex y coordinates exercise the ray-vertex rule
+    fp = synth.l_footprint_gap()
+    ys = np.unique(fp[:, 1])
+    xs = np.linspace(-0.5, 2.5, 301, dtype=np.float32)
+    pts = np.array([(x, y) for y in ys for x in xs], np.float32)
+    poses = np.zeros((1, 3), np.float32)
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.POLYGON, fp)
+    check(pts, poses, synth.POLYGON, fp, dg, mg, ag)
+
+
+def test_mask_padding_and_empty(ex):
+    g = np.random.default_rng(13)
+    pts = synth.uniform_points(g, 1500, -3.0, 3.0)
+    mask = (g.random(1500) > 0.3).astype(np.uint8)
+    poses = _poses(g, 20, 1.0)
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.POLYGON, synth.l_footprint(), mask=mask)
+    check(pts, poses, synth.POLYGON, synth.l_footprint(), dg, mg, ag, mask=mask)
+    assert np.all(np.isinf(dg[:, mask == 0]))
+    # all padding
+    z = np.zeros(1500, np.uint8)
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.POLYGON, synth.l_footprint(), mask=z)
+    assert np.all(np.isinf(dg)) and np.all(np.isinf(mg)) and np.all(ag == -1)
+
+
+def test_zero_and_one_point(ex):
+    import torch
+    poses = _poses(np.random.default_rng(14), 5)
+    f = ex.Footprint.polygon(synth.l_footprint())
+    _, m, a = ex.sdf_batch(torch.empty((0, 2), device="cuda"), _t(poses), f, dist=False)
+    torch.cuda.synchronize()
+    assert torch.all(torch.isinf(m)) and torch.all(a == -1)
+    pts = np.array([[0.7, -0.2]], np.float32)
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.POLYGON, synth.l_footprint())
+    check(pts, poses, synth.POLYGON, synth.l_footprint(), dg, mg, ag)
+
+
+def test_split_points_with_and_without_context(ex):
+    # few poses, many points: the points of one pose spread over many blocks
+    g = np.random.default_rng(15)
+    pts = synth.uniform_points(g, 50001, -6.0, 6.0)
+    poses = _poses(g, 3)
+    fp = synth.star_polygon(g, 17, 0.3, 1.2)
+    ctx = ex.Context()
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.POLYGON, fp, ctx=ctx)
+    check(pts, poses, synth.POLYGON, fp, dg, mg, ag)
+    _, mg2, ag2 = run_gpu(ex, pts, poses, synth.POLYGON, fp, ctx=ctx, dist=False)
+    np.testing.assert_array_equal(mg2, mg)
+    np.testing.assert_array_equal(ag2, ag)
+    _, mg3, ag3 = run_gpu(ex, pts, poses, synth.POLYGON, fp, ctx=None, dist=False)
+    np.testing.assert_array_equal(mg3, mg)
+    np.testing.assert_array_equal(ag3, ag)
+
+
+def test_nonfinite_points_do_not_win_the_minimum(ex):
+    g = np.random.default_rng(16)
+    pts = synth.uniform_points(g, 64, -2.0, 2.0)
+    pts[5] = (np.nan, 0.0)
+    pts[9] = (np.inf, -np.inf)
+    poses = _poses(g, 4, 0.5)
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.POLYGON, synth.l_footprint())
+    assert np.all(np.isfinite(mg)) and not np.any(np.isin(ag, [5, 9]))
+
+
+def test_full_size_microbench_sampled_rows(ex):
+    """16,384 poses x 8,192 points x 32-gon in the launch the benchmark times;
+    64 sampled rows against the oracle, every row's min/argmin consistent."""
+    w = synth.sdf_microbench(seed=0)
+    ctx = ex.Context()
+    dg, mg, ag = run_gpu(ex, w["points"], w["poses"], w["kind"], w["fp"], ctx=ctx)
+    rows = np.random.default_rng(0).choice(w["poses"].shape[0], 64, replace=False)
+    check(w["points"], w["poses"], w["kind"], w["fp"], dg, mg, ag, rows=rows)
+    np.testing.assert_array_equal(mg, dg.min(axis=1))
+    np.testing.assert_array_equal(dg[np.arange(dg.shape[0]), ag], mg)
