@@ -67,7 +67,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
         return self
@@ -226,6 +226,43 @@ def mppi_extra(torch, ex, dev):
     return out
 
 
+def run_mppi_workload(args):
+    """Time one MPPI cycle workload (plain_step or forklift) as plain launches."""
+    import torch
+
+    import paper_2605_29663_gb300 as ex
+    import synth
+    from paper_2605_29663_gb300 import build as _build
+    _build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    s = synth.plain_step(0) if args.workload == "plain_step" else synth.forklift(0)
+    p = s["params"]
+    fp = ex.Footprint(s["kind"], s["fp"])
+    t = {k: torch.from_numpy(s[k]).to(dev) for k in ("q0", "cloud", "waypoints", "U", "eps")}
+    mask = torch.from_numpy(s["mask"]).to(dev) if s["mask"] is not None else None
+    ctx = ex.Context()
+    ctx.reserve(0, p["K"], p["T"])
+    outs = {}
+    for _ in range(args.warmup):
+        outs.update(ex.mppi_step(ctx, t["q0"], t["cloud"], t["waypoints"], t["U"], t["eps"], fp, p, mask=mask,
+                                 out=outs))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ex.mppi_step(ctx, t["q0"], t["cloud"], t["waypoints"], t["U"], t["eps"], fp, p, mask=mask, out=outs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": "MPPI steps/s", "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": args.workload, "K": p["K"], "T": p["T"], "N": s["cloud"].shape[0]},
+                      "gpu_launches": 3 * args.steps}), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -362,17 +399,21 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extra", action="store_true", help="skip the MPPI cycle measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target length of the CPU oracle sample")
+    ap.add_argument("--workload", choices=["sdf", "plain_step", "forklift"], default="sdf",
+                    help="sdf (headline) or one MPPI cycle workload timed on its own")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "sdf":
+        return run_mppi_workload(args)
     return run_gpu(args)
 
 

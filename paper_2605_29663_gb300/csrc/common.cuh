@@ -57,43 +57,64 @@ __device__ __forceinline__ void body_frame(float ox, float oy, float tx, float t
 // is the sign bit of dy_b * dy_{b+1}; the crossing abscissa test
 // p_x < v_bx + dy_b e_bx / e_by is the sign of g = dy_b k_b - dx_b being
 // clear.  Both ends of a vertex use the same dy, so the parity is consistent.
-// One edge b (compile-time index, so every footprint term is an immediate
-// constant-bank operand); recursion unrolls all E edges.
+// Three-input minimum (one instruction on sm_100-class GPUs).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 struct PolyAcc {
     float dxa0, dya0, dxa1, dya1;   // p - v_b for the two points
     float mm0, mm1;                 // running min of d_seg^2
     unsigned ss0, ss1;              // crossing parity (sign bit)
 };
 
+// Edge B (a compile-time index, so every footprint term is an immediate
+// constant-bank operand) for both points; returns the two squared segment
+// distances and advances the vertex differences to v_{B+1}.
+template <int E, int B>
+__device__ __forceinline__ void poly_edge(const PolyC<E> &P, float px0, float py0, float px1, float py1,
+                                          const PolyAcc &z, PolyAcc &a, float &q0, float &q1) {
+    float dxb0, dyb0, dxb1, dyb1;
+    if constexpr (B + 1 < E) {
+        dxb0 = px0 - P.vx[B + 1]; dyb0 = py0 - P.vy[B + 1];
+        dxb1 = px1 - P.vx[B + 1]; dyb1 = py1 - P.vy[B + 1];
+    } else {
+        dxb0 = z.dxa0; dyb0 = z.dya0; dxb1 = z.dxa1; dyb1 = z.dya1;
+    }
+    const float t0 = __saturatef(fmaf(a.dya0, P.eyn[B], a.dxa0 * P.exn[B]));
+    const float t1 = __saturatef(fmaf(a.dya1, P.eyn[B], a.dxa1 * P.exn[B]));
+    const float qx0 = fmaf(-t0, P.ex[B], a.dxa0), qy0 = fmaf(-t0, P.ey[B], a.dya0);
+    const float qx1 = fmaf(-t1, P.ex[B], a.dxa1), qy1 = fmaf(-t1, P.ey[B], a.dya1);
+    q0 = fmaf(qy0, qy0, qx0 * qx0);
+    q1 = fmaf(qy1, qy1, qx1 * qx1);
+    const float g0 = fmaf(a.dya0, P.kx[B], -a.dxa0), g1 = fmaf(a.dya1, P.kx[B], -a.dxa1);
+    const float X0 = a.dya0 * dyb0, X1 = a.dya1 * dyb1;
+    a.ss0 ^= __float_as_uint(X0) & ~__float_as_uint(g0);
+    a.ss1 ^= __float_as_uint(X1) & ~__float_as_uint(g1);
+    a.dxa0 = dxb0; a.dya0 = dyb0; a.dxa1 = dxb1; a.dya1 = dyb1;
+}
+
+// Edges B and B+1 (E is even), folded into the running minimum with one
+// three-input min per point; recursion unrolls all E edges.
 template <int E, int B>
 __device__ __forceinline__ void poly_edges(const PolyC<E> &P, float px0, float py0, float px1, float py1,
                                            const PolyAcc &z, PolyAcc &a) {
     if constexpr (B < E) {
-        float dxb0, dyb0, dxb1, dyb1;
-        if constexpr (B + 1 < E) {
-            dxb0 = px0 - P.vx[B + 1]; dyb0 = py0 - P.vy[B + 1];
-            dxb1 = px1 - P.vx[B + 1]; dyb1 = py1 - P.vy[B + 1];
-        } else {
-            dxb0 = z.dxa0; dyb0 = z.dya0; dxb1 = z.dxa1; dyb1 = z.dya1;
-        }
-        const float t0 = __saturatef(fmaf(a.dya0, P.eyn[B], a.dxa0 * P.exn[B]));
-        const float t1 = __saturatef(fmaf(a.dya1, P.eyn[B], a.dxa1 * P.exn[B]));
-        const float qx0 = fmaf(-t0, P.ex[B], a.dxa0), qy0 = fmaf(-t0, P.ey[B], a.dya0);
-        const float qx1 = fmaf(-t1, P.ex[B], a.dxa1), qy1 = fmaf(-t1, P.ey[B], a.dya1);
-        a.mm0 = fminf(a.mm0, fmaf(qy0, qy0, qx0 * qx0));
-        a.mm1 = fminf(a.mm1, fmaf(qy1, qy1, qx1 * qx1));
-        const float g0 = fmaf(a.dya0, P.kx[B], -a.dxa0), g1 = fmaf(a.dya1, P.kx[B], -a.dxa1);
-        const float X0 = a.dya0 * dyb0, X1 = a.dya1 * dyb1;
-        a.ss0 ^= __float_as_uint(X0) & ~__float_as_uint(g0);
-        a.ss1 ^= __float_as_uint(X1) & ~__float_as_uint(g1);
-        a.dxa0 = dxb0; a.dya0 = dyb0; a.dxa1 = dxb1; a.dya1 = dyb1;
-        poly_edges<E, B + 1>(P, px0, py0, px1, py1, z, a);
+        float qa0, qa1, qb0, qb1;
+        poly_edge<E, B>(P, px0, py0, px1, py1, z, a, qa0, qa1);
+        poly_edge<E, B + 1>(P, px0, py0, px1, py1, z, a, qb0, qb1);
+        a.mm0 = fmin3(a.mm0, qa0, qb0);
+        a.mm1 = fmin3(a.mm1, qa1, qb1);
+        poly_edges<E, B + 2>(P, px0, py0, px1, py1, z, a);
     }
 }
 
 template <int E>
 __device__ __forceinline__ void poly_eval2(const PolyC<E> &P, float px0, float py0, float px1, float py1,
                                            float &m0, float &m1, unsigned &s0, unsigned &s1) {
+    static_assert(E % 2 == 0, "edge count is padded to an even number");
     PolyAcc z;
     z.dxa0 = px0 - P.vx[0]; z.dya0 = py0 - P.vy[0];
     z.dxa1 = px1 - P.vx[0]; z.dya1 = py1 - P.vy[0];
@@ -104,32 +125,34 @@ __device__ __forceinline__ void poly_eval2(const PolyC<E> &P, float px0, float p
     m0 = a.mm0; m1 = a.mm1; s0 = a.ss0; s1 = a.ss1;
 }
 
-// Signed squared distance (negative inside): monotone in the signed distance.
-__device__ __forceinline__ float poly_key(float m, unsigned s) {
-    return (s & 0x80000000u) ? -m : m;
-}
-__device__ __forceinline__ float poly_dist(float m, unsigned s) {
-    const float r = sqrtf(m);
-    return (s & 0x80000000u) ? -r : r;
-}
-__device__ __forceinline__ float poly_key_to_dist(float key) {
-    return key < 0.f ? -sqrtf(-key) : sqrtf(key);
-}
-
 // ---------------------------------------------------------------- rect cover
 // Sec. IV-C.2: d_box = |max(a,0)| + min(max(a_x,a_y),0), a = |p - c| - s, and
 // d_rect = min_j d_box.  For every box one of the two terms is zero, so
 // min_j d_box = sqrt(min_j |max(a_j,0)|^2) + min(min_j max(a_jx,a_jy), 0)
 // exactly (sqrt is correctly rounded, hence monotone).
 template <int R, int J>
+__device__ __forceinline__ void rect_box(const RectC<R> &Q, float px, float py, float &n2, float &mx2) {
+    const float ax = fabsf(px - Q.cx[J]) - Q.sx[J];
+    const float ay = fabsf(py - Q.cy[J]) - Q.sy[J];
+    const float mx = fmaxf(ax, 0.f), my = fmaxf(ay, 0.f);
+    n2 = fmaf(my, my, mx * mx);
+    mx2 = fmaxf(ax, ay);
+}
+
+template <int R, int J>
 __device__ __forceinline__ void rect_boxes(const RectC<R> &Q, float px, float py, float &nn, float &in) {
-    if constexpr (J < R) {
-        const float ax = fabsf(px - Q.cx[J]) - Q.sx[J];
-        const float ay = fabsf(py - Q.cy[J]) - Q.sy[J];
-        const float mx = fmaxf(ax, 0.f), my = fmaxf(ay, 0.f);
-        nn = fminf(nn, fmaf(my, my, mx * mx));
-        in = fminf(in, fmaxf(ax, ay));
-        rect_boxes<R, J + 1>(Q, px, py, nn, in);
+    if constexpr (J + 1 < R) {
+        float na, ia, nb, ib;
+        rect_box<R, J>(Q, px, py, na, ia);
+        rect_box<R, J + 1>(Q, px, py, nb, ib);
+        nn = fmin3(nn, na, nb);
+        in = fmin3(in, ia, ib);
+        rect_boxes<R, J + 2>(Q, px, py, nn, in);
+    } else if constexpr (J < R) {
+        float na, ia;
+        rect_box<R, J>(Q, px, py, na, ia);
+        nn = fminf(nn, na);
+        in = fminf(in, ia);
     }
 }
 
@@ -181,17 +204,19 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 
 namespace exact {
 
-// Uniform evaluation interface over the two footprint kinds: signed distance
-// d and order key of two body-frame points (the key is monotone in d and is
-// what minima are taken over; key_to_dist maps a key back to d exactly).
+// Uniform evaluation interface over the two footprint kinds.  For two
+// body-frame points it yields the order key (monotone in the signed
+// distance: the signed squared distance for polygons, the signed depth or
+// squared distance for rectangle covers) and, when asked, the signed
+// distance itself.  key_to_dist maps a key back to the same distance.
 template <int E>
 __device__ __forceinline__ void eval2(const PolyC<E> &P, float px0, float py0, float px1, float py1,
                                       float &k0, float &k1) {
     float m0, m1;
     unsigned s0, s1;
     poly_eval2(P, px0, py0, px1, py1, m0, m1, s0, s1);
-    k0 = poly_key(m0, s0);
-    k1 = poly_key(m1, s1);
+    k0 = __uint_as_float(__float_as_uint(m0) | (s0 & 0x80000000u));
+    k1 = __uint_as_float(__float_as_uint(m1) | (s1 & 0x80000000u));
 }
 template <int R>
 __device__ __forceinline__ void eval2(const RectC<R> &Q, float px0, float py0, float px1, float py1,
@@ -202,8 +227,12 @@ __device__ __forceinline__ void eval2(const RectC<R> &Q, float px0, float py0, f
     k0 = rect_key(n0, i0);
     k1 = rect_key(n1, i1);
 }
+// Signed squared distance key -> signed distance (sign bit carried over).
 template <int E>
-__device__ __forceinline__ float key_to_dist(const PolyC<E> &, float key) { return poly_key_to_dist(key); }
+__device__ __forceinline__ float key_to_dist(const PolyC<E> &, float key) {
+    const unsigned b = __float_as_uint(key);
+    return __uint_as_float(__float_as_uint(sqrtf(__uint_as_float(b & 0x7fffffffu))) | (b & 0x80000000u));
+}
 template <int R>
 __device__ __forceinline__ float key_to_dist(const RectC<R> &, float key) { return rect_key_to_dist(key); }
 

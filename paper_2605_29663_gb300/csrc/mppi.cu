@@ -52,38 +52,55 @@ static MppiScratch carve(void *base, int K, int T) {
     return s;
 }
 
-// Per-step minimum over all points of the body-frame key, for the poses in
-// shared memory; each block thread walks point pairs, warps meet in
-// shared-memory atomics on order-preserving keys.
-template <class FPC>
+constexpr int kPairsPerLane = 4;   // point pairs one lane evaluates per work item
+
+// Per-step minimum over all points of the body-frame key for the T poses in
+// shared memory.  Work items (step h, chunk of 32 * kPairsPerLane point
+// pairs) are dealt to the block's warps round-robin; each item ends in one
+// warp shuffle-min and one shared-memory atomicMin on the order-preserving
+// key of step h.  A ragged last pair duplicates its first point (same key).
+template <class FPC, bool MASKED>
 __device__ __forceinline__ void steps_min_keys(const FPC &fpc, const float2 *__restrict__ pts,
                                                const uint8_t *__restrict__ mask, int N, const float4 *pose,
                                                int T, unsigned *keyh) {
     const int npairs = (N + 1) >> 1;
-    for (int h = 0; h < T; ++h) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    constexpr int span = 32 * kPairsPerLane;
+    const int nchunk = npairs > 0 ? (npairs + span - 1) / span : 0;
+    const int items = T * nchunk;
+    for (int it = warp; it < items; it += nwarps) {
+        const int h = it / nchunk, c = it - h * nchunk;
         const float4 q = pose[h];
         float best = finf();
-        for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
-            const int i0 = 2 * j, i1 = 2 * j + 1;
-            const bool has1 = i1 < N;
+        const int jend = min(npairs, (c + 1) * span);
+        for (int j = c * span + lane; j < jend; j += 32) {
+            const int i0 = 2 * j, i1 = min(2 * j + 1, N - 1);
             const float2 o0 = __ldg(pts + i0);
-            const float2 o1 = has1 ? __ldg(pts + i1) : o0;
+            const float2 o1 = __ldg(pts + i1);
             float px0, py0, px1, py1;
             body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
             body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
             float k0, k1;
             eval2(fpc, px0, py0, px1, py1, k0, k1);
-            const bool v0 = mask ? __ldg(mask + i0) != 0 : true;
-            const bool v1 = has1 && (mask ? __ldg(mask + i1) != 0 : true);
-            if (v0) best = fminf(best, k0);   // fminf ignores a NaN key
-            if (v1) best = fminf(best, k1);
+            if (MASKED) {
+                k0 = __ldg(mask + i0) ? k0 : finf();
+                k1 = __ldg(mask + i1) ? k1 : finf();
+            }
+            best = fmin3(best, k0, k1);
         }
         best = warp_min_f(best);
-        if ((threadIdx.x & 31) == 0) atomicMin(keyh + h, f2ord(best));
+        if (lane == 0) atomicMin(keyh + h, f2ord(best));
     }
 }
 
-template <class FPC>
+// phi_obs (Sec. IV-E) in double: its terms are large (w_coll, w_inf scale)
+// and are summed over the horizon.
+__device__ __forceinline__ double phi_obs_d(const MppiP &P, float d) {
+    const double gap = fmax((double)P.d_safe - (double)d, 0.0);
+    return (d < 0.f ? (double)P.w_coll : 0.0) + (double)P.w_rep * gap * gap;
+}
+
+template <class FPC, bool MASKED>
 __global__ void __launch_bounds__(kBlock)
 mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state,
                    const float2 *__restrict__ pts, const uint8_t *__restrict__ mask, int N,
@@ -118,7 +135,7 @@ mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state
         if (lane == 0) s_term = P.w_term * guidance_dist(R.qTx, R.qTy, wp, W);
     }
     __syncthreads();
-    steps_min_keys(fpc, pts, mask, N, s_pose, T, s_key);
+    steps_min_keys<FPC, MASKED>(fpc, pts, mask, N, s_pose, T, s_key);
     __syncthreads();
     if (threadIdx.x < 32) {
         double acc = 0.0;
@@ -128,7 +145,7 @@ mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state
             const float key = ord2f(k);
             const float d = key == finf() ? finf() : key_to_dist(fpc, key);
             if (dmin_out) dmin_out[(size_t)r * T + h] = d;
-            acc += (double)s_stage[h] + (double)phi_obs(P, d);
+            acc += (double)s_stage[h] + phi_obs_d(P, d);
             unsafe |= d < P.d_safe;
         }
 #pragma unroll
@@ -356,8 +373,8 @@ extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud,
     const int chunks = npairs > chunk_pairs ? (npairs + chunk_pairs - 1) / chunk_pairs : 1;
     return with_footprint(fp, [&](auto fpc) -> int {
         using FPC = decltype(fpc);
-        mppi_sample_kernel<FPC><<<P.K, kBlock, 0, st>>>(P, fpc, state, pts, mask, n_points, waypoints, n_wp, U,
-                                                        noise, S.J, S.chi, dmin);
+        auto ka = mask ? mppi_sample_kernel<FPC, true> : mppi_sample_kernel<FPC, false>;
+        ka<<<P.K, kBlock, 0, st>>>(P, fpc, state, pts, mask, n_points, waypoints, n_wp, U, noise, S.J, S.chi, dmin);
         mppi_update_kernel<<<1, kUpdBlock, 0, st>>>(P, state, U, noise, S, costs, weights, U_upd);
         mppi_validate_kernel<FPC><<<P.T * chunks, kBlock, 0, st>>>(P, fpc, pts, mask, n_points, chunks,
                                                                    chunk_pairs, S, U, u_star, valid);

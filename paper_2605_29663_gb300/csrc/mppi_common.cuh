@@ -73,12 +73,6 @@ __device__ __forceinline__ float guidance_dist(float x, float y, const float *__
     return sqrtf(best);
 }
 
-// phi_obs (Sec. IV-E).
-__device__ __forceinline__ float phi_obs(const MppiP &P, float d) {
-    const float gap = fmaxf(P.d_safe - d, 0.f);
-    return (d < 0.f ? P.w_coll : 0.f) + P.w_rep * gap * gap;
-}
-
 // Warp-parallel forward-Euler rollout (Sec. III-D).  Lane l holds steps
 // h = l*per .. l*per+per-1 (blocked).  Because the heading rate depends only
 // on the control, theta_h is a prefix sum of rate*dt, and x, y are prefix

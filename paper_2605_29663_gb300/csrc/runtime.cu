@@ -70,14 +70,14 @@ int check_simple(const double *v, int n) {
 }
 
 int poly_bucket(int n) {
-    static const int sizes[] = {4, 8, 12, 16, 24, 32, 40, 48, 56, 64};
+    static const int sizes[] = {4, 6, 8, 10, 12, 14, 16, 24, 32, 40, 48, 56, 64};
     for (int s : sizes)
         if (n <= s) return s;
     return -1;
 }
 
 int rect_bucket(int n) {
-    static const int sizes[] = {1, 2, 4, 8};
+    static const int sizes[] = {1, 2, 3, 4, 5, 6, 7, 8};
     for (int s : sizes)
         if (n <= s) return s;
     return -1;

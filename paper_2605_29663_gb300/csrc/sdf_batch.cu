@@ -13,7 +13,7 @@
 
 namespace exact {
 
-template <class FPC, bool DIST>
+template <class FPC, bool DIST, bool MASKED>
 __global__ void __launch_bounds__(kBlock)
 sdf_batch_kernel(const float2 *__restrict__ pts, const uint8_t *__restrict__ mask, int N,
                  const float *__restrict__ poses, const FPC fpc, float *__restrict__ dist, int vec_store,
@@ -21,14 +21,15 @@ sdf_batch_kernel(const float2 *__restrict__ pts, const uint8_t *__restrict__ mas
                  unsigned long long *__restrict__ keys, int chunks, int chunk_pairs) {
     const int pose = blockIdx.x / chunks;
     const int chunk = blockIdx.x - pose * chunks;
-    const float tx = poses[3 * pose], ty = poses[3 * pose + 1], th = poses[3 * pose + 2];
+    const float tx = poses[3 * (size_t)pose], ty = poses[3 * (size_t)pose + 1], th = poses[3 * (size_t)pose + 2];
     float sn, cs;
     sincosf(th, &sn, &cs);
     const int npairs = (N + 1) >> 1;
     const int pbeg = chunk * chunk_pairs;
     const int pend = min(npairs, pbeg + chunk_pairs);
     float *drow = DIST ? dist + (size_t)pose * (size_t)N : nullptr;
-    unsigned long long best = kNoKey;
+    float bk = finf();        // best key of this thread (first index wins ties)
+    int bi = -1;
 
     for (int j = pbeg + (int)threadIdx.x; j < pend; j += kBlock) {
         const int i0 = 2 * j, i1 = 2 * j + 1;
@@ -40,11 +41,16 @@ sdf_batch_kernel(const float2 *__restrict__ pts, const uint8_t *__restrict__ mas
         body_frame(o1.x, o1.y, tx, ty, cs, sn, px1, py1);
         float k0, k1;
         eval2(fpc, px0, py0, px1, py1, k0, k1);
-        const bool v0 = mask ? __ldg(mask + i0) != 0 : true;
-        const bool v1 = has1 && (mask ? __ldg(mask + i1) != 0 : true);
+        bool v0 = true, v1 = has1;
+        if (MASKED) {
+            v0 = __ldg(mask + i0) != 0;
+            v1 = has1 && __ldg(mask + i1) != 0;
+            k0 = v0 ? k0 : finf();
+            k1 = v1 ? k1 : finf();
+        }
         if (DIST) {
-            const float d0 = v0 ? key_to_dist(fpc, k0) : finf();
-            const float d1 = v1 ? key_to_dist(fpc, k1) : finf();
+            const float d0 = key_to_dist(fpc, k0);
+            const float d1 = key_to_dist(fpc, k1);
             if (vec_store) {
                 __stcs(reinterpret_cast<float2 *>(drow) + j, make_float2(d0, d1));
             } else {
@@ -52,13 +58,15 @@ sdf_batch_kernel(const float2 *__restrict__ pts, const uint8_t *__restrict__ mas
                 if (has1) __stcs(drow + i1, d1);
             }
         }
-        // NaN keys (non-finite input) never win the minimum
-        if (v0 && k0 == k0) { const unsigned long long w = pack_key(k0, (unsigned)i0); best = w < best ? w : best; }
-        if (v1 && k1 == k1) { const unsigned long long w = pack_key(k1, (unsigned)i1); best = w < best ? w : best; }
+        // strict "<" keeps the lowest index among equal keys; +inf (padding)
+        // and NaN never replace the initial +inf
+        if (k0 < bk) { bk = k0; bi = i0; }
+        if (v1 && k1 < bk) { bk = k1; bi = i1; }
     }
 
     if (!dmin && !argmin) return;
     __shared__ unsigned long long red[kBlock / 32];
+    unsigned long long best = bi < 0 ? kNoKey : pack_key(bk, (unsigned)bi);
     best = warp_min_u64(best);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
     __syncthreads();
@@ -133,12 +141,10 @@ extern "C" int exact_sdf_batch(exact_ctx *ctx, const float *points, const uint8_
     const unsigned grid = (unsigned)(n_poses * chunks);
     return with_footprint(fp, [&](auto fpc) -> int {
         using FPC = decltype(fpc);
-        if (dist)
-            sdf_batch_kernel<FPC, true><<<grid, kBlock, 0, st>>>(p2, mask, n_points, poses, fpc, dist, vec, dmin,
-                                                                argmin, keys, chunks, chunk_pairs);
-        else
-            sdf_batch_kernel<FPC, false><<<grid, kBlock, 0, st>>>(p2, mask, n_points, poses, fpc, dist, vec, dmin,
-                                                                 argmin, keys, chunks, chunk_pairs);
+        auto k = mask ? (dist ? sdf_batch_kernel<FPC, true, true> : sdf_batch_kernel<FPC, false, true>)
+                      : (dist ? sdf_batch_kernel<FPC, true, false> : sdf_batch_kernel<FPC, false, false>);
+        k<<<grid, kBlock, 0, st>>>(p2, mask, n_points, poses, fpc, dist, vec, dmin, argmin, keys, chunks,
+                                   chunk_pairs);
         if (keys)
             sdf_keys_finish<FPC><<<(n_poses + 255) / 256, 256, 0, st>>>(keys, n_poses, fpc, dmin, argmin);
         return cuda_status(cudaGetLastError());
