@@ -129,13 +129,16 @@ __device__ __forceinline__ void poly_eval2(const PolyC<E> &P, float px0, float p
 // Sec. IV-C.2: d_box = |max(a,0)| + min(max(a_x,a_y),0), a = |p - c| - s, and
 // d_rect = min_j d_box.  For every box one of the two terms is zero, so
 // min_j d_box = sqrt(min_j |max(a_j,0)|^2) + min(min_j max(a_jx,a_jy), 0)
-// exactly (sqrt is correctly rounded, hence monotone).
+// exactly (sqrt is correctly rounded, hence monotone).  The clamp is taken
+// as a + |a| = 2 max(a, 0) (an add with an absolute-value operand, exact),
+// so the evaluator tracks 4 |max(a,0)|^2 and halves the root at the end:
+// both scalings by powers of two are exact.
 template <int R, int J>
-__device__ __forceinline__ void rect_box(const RectC<R> &Q, float px, float py, float &n2, float &mx2) {
+__device__ __forceinline__ void rect_box(const RectC<R> &Q, float px, float py, float &n4, float &mx2) {
     const float ax = fabsf(px - Q.cx[J]) - Q.sx[J];
     const float ay = fabsf(py - Q.cy[J]) - Q.sy[J];
-    const float mx = fmaxf(ax, 0.f), my = fmaxf(ay, 0.f);
-    n2 = fmaf(my, my, mx * mx);
+    const float ux = ax + fabsf(ax), uy = ay + fabsf(ay);
+    n4 = fmaf(uy, uy, ux * ux);
     mx2 = fmaxf(ax, ay);
 }
 
@@ -156,17 +159,17 @@ __device__ __forceinline__ void rect_boxes(const RectC<R> &Q, float px, float py
     }
 }
 
+// n4 = min_j 4 |max(a_j, 0)|^2, inner = min_j max(a_jx, a_jy).
 template <int R>
-__device__ __forceinline__ void rect_eval(const RectC<R> &Q, float px, float py, float &n2, float &inner) {
+__device__ __forceinline__ void rect_eval(const RectC<R> &Q, float px, float py, float &n4, float &inner) {
     float nn = finf(), in = finf();
     rect_boxes<R, 0>(Q, px, py, nn, in);
-    n2 = nn;
+    n4 = nn;
     inner = in;
 }
-// Mixed key: the (negative) depth inside, the squared distance outside.
-__device__ __forceinline__ float rect_key(float n2, float inner) { return inner < 0.f ? inner : n2; }
-__device__ __forceinline__ float rect_dist(float n2, float inner) { return sqrtf(n2) + fminf(inner, 0.f); }
-__device__ __forceinline__ float rect_key_to_dist(float key) { return key < 0.f ? key : sqrtf(key); }
+// Mixed key: the (negative) depth inside, 4 x the squared distance outside.
+__device__ __forceinline__ float rect_key(float n4, float inner) { return inner < 0.f ? inner : n4; }
+__device__ __forceinline__ float rect_key_to_dist(float key) { return key < 0.f ? key : 0.5f * sqrtf(key); }
 
 // ---------------------------------------------------------------- keys
 // Order-preserving float <-> uint32 map (total order, -0 < +0).

@@ -1,38 +1,51 @@
 // mppi.cu -- mppi_step: one batched EXACT-MPPI control cycle (Algorithm 1).
 //
 // Three kernels, stream-ordered (and capturable in one CUDA graph):
-//   A  mppi_sample_kernel   one block per sample r: warp-parallel rollout,
-//                           then every (step, point) body-frame signed
-//                           distance with per-step minima in shared memory,
-//                           then phi_task + phi_ctrl + phi_obs, chi and J.
-//   B1 mppi_update_kernel   one block: beta = min J~, the softmax weights, U += sum_r omega_r eps_r, and the
-//                           rollout of the updated nominal.
+//   A  mppi_sample_kernel   one block per sample r: warp 0 rolls the sample
+//                           out (two warp prefix scans) while the other warps
+//                           stage the obstacle points in shared memory; then
+//                           every (step, point) body-frame signed distance
+//                           with per-step minima in shared memory; then
+//                           phi_task + phi_ctrl + phi_obs (double), chi, J.
+//   B1 mppi_update_kernel   ceil(K / 128) blocks: beta = min J~ (each block
+//                           reduces all K in double), the softmax weights of
+//                           its samples and their weighted clipped noise; the
+//                           last block (atomic ticket) sums the partials,
+//                           writes U_upd and rolls the updated nominal out.
 //   B2 mppi_validate_kernel one block per (step, point chunk) of the nominal:
-//                           d_min >= d_safe; the last block to finish (atomic
-//                           ticket, no waiting) writes u*, the shifted or
-//                           reset U and the valid flag.
-// No K x T x N intermediate touches memory; the only scratch is per-sample
-// J / chi and per-step nominal data in the context arena.
+//                           d_min >= d_safe; the last block writes u*, the
+//                           shifted or reset U and the valid flag.
+// No K x T x N intermediate touches memory; the scratch is per-sample J /
+// chi / weights, per-block partial sums and per-step nominal data in the
+// context arena.  No block ever waits for another (tickets only).
 #include "internal.h"
 #include "mppi_common.cuh"
 
 namespace exact {
 
+constexpr int kUpdChunk = 128;    // samples per update block
+constexpr int kUpdBlock = 256;
+constexpr int kStage = 4096;      // obstacle points staged in shared memory per pass
+
 struct MppiScratch {
     double *J;          // K
     int *chi;           // K
     float *wt;          // K   unnormalised weights exp(-(J~ - beta)/lambda)
+    float *part;        // G x (T*nu + 1)   per-block weighted noise sums and Z
     float *U_upd;       // T x nu
     float4 *nom_pose;   // T   scored nominal states (x, y, cos, sin)
     int *bad;           // 1   validation failed
-    unsigned *ticket;   // 1   finished validation blocks
+    unsigned *ticket;   // 2   finished update / validation blocks
 };
+
+static int upd_blocks(int K) { return (K + kUpdChunk - 1) / kUpdChunk; }
 
 size_t mppi_scratch_bytes(int K, int T) {
     size_t b = 0;
     b += align_up((size_t)K * sizeof(double), 256);
     b += align_up((size_t)K * sizeof(int), 256);
     b += align_up((size_t)K * sizeof(float), 256);
+    b += align_up((size_t)upd_blocks(K) * (T * 3 + 1) * sizeof(float), 256);
     b += align_up((size_t)T * 3 * sizeof(float), 256);
     b += align_up((size_t)T * sizeof(float4), 256);
     b += 256 + 256;
@@ -45,6 +58,7 @@ static MppiScratch carve(void *base, int K, int T) {
     s.J = reinterpret_cast<double *>(p); p += align_up((size_t)K * sizeof(double), 256);
     s.chi = reinterpret_cast<int *>(p); p += align_up((size_t)K * sizeof(int), 256);
     s.wt = reinterpret_cast<float *>(p); p += align_up((size_t)K * sizeof(float), 256);
+    s.part = reinterpret_cast<float *>(p); p += align_up((size_t)upd_blocks(K) * (T * 3 + 1) * sizeof(float), 256);
     s.U_upd = reinterpret_cast<float *>(p); p += align_up((size_t)T * 3 * sizeof(float), 256);
     s.nom_pose = reinterpret_cast<float4 *>(p); p += align_up((size_t)T * sizeof(float4), 256);
     s.bad = reinterpret_cast<int *>(p); p += 256;
@@ -54,16 +68,18 @@ static MppiScratch carve(void *base, int K, int T) {
 
 constexpr int kPairsPerLane = 4;   // point pairs one lane evaluates per work item
 
-// Per-step minimum over all points of the body-frame key for the T poses in
-// shared memory.  Work items (step h, chunk of 32 * kPairsPerLane point
-// pairs) are dealt to the block's warps round-robin; each item ends in one
-// warp shuffle-min and one shared-memory atomicMin on the order-preserving
-// key of step h.  A ragged last pair duplicates its first point (same key).
-template <class FPC, bool MASKED>
-__device__ __forceinline__ void steps_min_keys(const FPC &fpc, const float2 *__restrict__ pts,
-                                               const uint8_t *__restrict__ mask, int N, const float4 *pose,
+// Per-step minimum of the body-frame key over n staged points for the T
+// poses in shared memory.  Work items (step h, chunk of 32 * kPairsPerLane
+// point pairs) are dealt to the block's warps round-robin; each item ends in
+// one warp shuffle-min and one shared-memory atomicMin on the
+// order-preserving key of step h.  A ragged last pair repeats its first
+// point.  Masked points were staged as NaN, which every evaluator turns into
+// a +inf key (NaN terms are dropped by min, and the canonical NaN has a
+// clear sign bit, so it never toggles the crossing parity).
+template <class FPC>
+__device__ __forceinline__ void steps_min_keys(const FPC &fpc, const float2 *pts, int n, const float4 *pose,
                                                int T, unsigned *keyh) {
-    const int npairs = (N + 1) >> 1;
+    const int npairs = (n + 1) >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     constexpr int span = 32 * kPairsPerLane;
     const int nchunk = npairs > 0 ? (npairs + span - 1) / span : 0;
@@ -74,22 +90,28 @@ __device__ __forceinline__ void steps_min_keys(const FPC &fpc, const float2 *__r
         float best = finf();
         const int jend = min(npairs, (c + 1) * span);
         for (int j = c * span + lane; j < jend; j += 32) {
-            const int i0 = 2 * j, i1 = min(2 * j + 1, N - 1);
-            const float2 o0 = __ldg(pts + i0);
-            const float2 o1 = __ldg(pts + i1);
+            const float2 o0 = pts[2 * j];
+            const float2 o1 = pts[min(2 * j + 1, n - 1)];
             float px0, py0, px1, py1;
             body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
             body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
             float k0, k1;
             eval2(fpc, px0, py0, px1, py1, k0, k1);
-            if (MASKED) {
-                k0 = __ldg(mask + i0) ? k0 : finf();
-                k1 = __ldg(mask + i1) ? k1 : finf();
-            }
             best = fmin3(best, k0, k1);
         }
         best = warp_min_f(best);
         if (lane == 0) atomicMin(keyh + h, f2ord(best));
+    }
+}
+
+// Copy points [base, base + n) into shared memory, masked ones as NaN.
+__device__ __forceinline__ void stage_points(float2 *dst, const float2 *__restrict__ pts,
+                                             const uint8_t *__restrict__ mask, int base, int n, int t0, int nt) {
+    const float qnan = __int_as_float(0x7fffffff);
+    for (int i = t0; i < n; i += nt) {
+        float2 p = __ldg(pts + base + i);
+        if (mask && !__ldg(mask + base + i)) p = make_float2(qnan, qnan);
+        dst[i] = p;
     }
 }
 
@@ -100,13 +122,14 @@ __device__ __forceinline__ double phi_obs_d(const MppiP &P, float d) {
     return (d < 0.f ? (double)P.w_coll : 0.0) + (double)P.w_rep * gap * gap;
 }
 
-template <class FPC, bool MASKED>
+template <class FPC>
 __global__ void __launch_bounds__(kBlock)
 mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state,
                    const float2 *__restrict__ pts, const uint8_t *__restrict__ mask, int N,
                    const float *__restrict__ wp, int W, const float *__restrict__ U,
                    const float *__restrict__ noise, double *__restrict__ Jout, int *__restrict__ chi_out,
                    float *__restrict__ dmin_out) {
+    extern __shared__ float2 s_pts[];            // min(N, kStage) staged points
     __shared__ float4 s_pose[EXACT_MAX_HORIZON];
     __shared__ float s_stage[EXACT_MAX_HORIZON];
     __shared__ unsigned s_key[EXACT_MAX_HORIZON];
@@ -115,6 +138,7 @@ mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state
     const int T = P.T, nu = P.nu;
     for (int h = threadIdx.x; h < T; h += blockDim.x) s_key[h] = f2ord(finf());
 
+    const int n0 = min(N, kStage);
     if (threadIdx.x < 32) {
         const float *eps = noise + (size_t)r * T * nu;
         LaneRollout R;
@@ -133,16 +157,24 @@ mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state
             }
         }
         if (lane == 0) s_term = P.w_term * guidance_dist(R.qTx, R.qTy, wp, W);
+    } else {
+        stage_points(s_pts, pts, mask, 0, n0, threadIdx.x - 32, blockDim.x - 32);
     }
     __syncthreads();
-    steps_min_keys<FPC, MASKED>(fpc, pts, mask, N, s_pose, T, s_key);
+    steps_min_keys(fpc, s_pts, n0, s_pose, T, s_key);
+    for (int base = kStage; base < N; base += kStage) {   // clouds larger than the stage
+        const int n = min(kStage, N - base);
+        __syncthreads();
+        stage_points(s_pts, pts, mask, base, n, threadIdx.x, blockDim.x);
+        __syncthreads();
+        steps_min_keys(fpc, s_pts, n, s_pose, T, s_key);
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
         double acc = 0.0;
         bool unsafe = false;
         for (int h = threadIdx.x; h < T; h += 32) {
-            const unsigned k = s_key[h];
-            const float key = ord2f(k);
+            const float key = ord2f(s_key[h]);
             const float d = key == finf() ? finf() : key_to_dist(fpc, key);
             if (dmin_out) dmin_out[(size_t)r * T + h] = d;
             acc += (double)s_stage[h] + phi_obs_d(P, d);
@@ -158,88 +190,102 @@ mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state
     }
 }
 
-constexpr int kUpdBlock = 1024;
-
-// B1: weights, update and nominal rollout (one block).
+// B1: block b owns samples [b * kUpdChunk, (b + 1) * kUpdChunk).  Every block
+// reduces beta = min_r J~_r over all K itself (J~ = J + w_inf I(chi) in
+// double, so the large offset costs no precision), forms the unnormalised
+// weights of its samples and their weighted clipped perturbations, and
+// leaves (sum w eps', sum w) in its partial slot.  The last block to finish
+// (atomic ticket) adds the partials, writes the normalised weights, costs
+// and U_upd, and rolls the updated nominal out for validation.
 __global__ void __launch_bounds__(kUpdBlock)
 mppi_update_kernel(const MppiP P, const float *__restrict__ state, const float *__restrict__ U,
                    const float *__restrict__ noise, MppiScratch S, float *__restrict__ costs,
                    float *__restrict__ weights, float *__restrict__ U_upd_out) {
-    __shared__ double s_J[32];
-    __shared__ float s_f[32];
-    __shared__ float s_part[kUpdBlock];
+    __shared__ double s_J[kUpdBlock / 32];
+    __shared__ float s_w[kUpdChunk];
+    __shared__ float s_f[kUpdBlock / 32];
     __shared__ float s_U[EXACT_MAX_HORIZON * 3];
+    __shared__ bool s_last;
     const int K = P.K, T = P.T, nu = P.nu, TN = T * nu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = blockIdx.x * kUpdChunk, r1 = min(K, r0 + kUpdChunk);
 
-    // beta = min_r J~_r, with J~ = J + w_inf I(chi) formed in double so that
-    // J~ - beta keeps the precision of J despite the large w_inf offset
     double bJ = __longlong_as_double(0x7ff0000000000000ll);
     for (int r = tid; r < K; r += kUpdBlock) bJ = fmin(bJ, S.J[r] + (double)P.w_inf * (double)S.chi[r]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bJ = fmin(bJ, __shfl_xor_sync(0xffffffffu, bJ, o));
     if (lane == 0) s_J[warp] = bJ;
     __syncthreads();
-    if (warp == 0) {
-        bJ = s_J[lane];
+    double beta = s_J[0];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bJ = fmin(bJ, __shfl_xor_sync(0xffffffffu, bJ, o));
-        if (lane == 0) s_J[0] = bJ;
-    }
-    __syncthreads();
-    const double beta = s_J[0];
+    for (int w = 1; w < kUpdBlock / 32; ++w) beta = fmin(beta, s_J[w]);
 
-    // unnormalised weights and their sum Z
     float z = 0.f;
-    for (int r = tid; r < K; r += kUpdBlock) {
+    for (int r = r0 + tid; r < r1; r += kUpdBlock) {
         const double diff = (S.J[r] + (double)P.w_inf * (double)S.chi[r]) - beta;
         const float w = expf(-(float)diff / P.lambda);
+        s_w[r - r0] = w;
         S.wt[r] = w;
         z += w;
     }
     z = warp_sum_f(z);
     if (lane == 0) s_f[warp] = z;
     __syncthreads();
+    float *part = S.part + (size_t)blockIdx.x * (TN + 1);
+    for (int e = tid; e < TN; e += kUpdBlock) {
+        const float ue = U[e];
+        const int j = e % nu;
+        float a0 = 0.f, a1 = 0.f;
+        int r = r0;
+        for (; r + 1 < r1; r += 2) {
+            const float e0 = noise[(size_t)r * TN + e], e1 = noise[(size_t)(r + 1) * TN + e];
+            a0 = fmaf(s_w[r - r0], P.clamp ? clamp_u(P, j, ue + e0) - ue : e0, a0);
+            a1 = fmaf(s_w[r + 1 - r0], P.clamp ? clamp_u(P, j, ue + e1) - ue : e1, a1);
+        }
+        if (r < r1) {
+            const float e0 = noise[(size_t)r * TN + e];
+            a0 = fmaf(s_w[r - r0], P.clamp ? clamp_u(P, j, ue + e0) - ue : e0, a0);
+        }
+        part[e] = a0 + a1;
+    }
+    if (tid == 0) {
+        float zb = 0.f;
+        for (int w = 0; w < kUpdBlock / 32; ++w) zb += s_f[w];
+        part[TN] = zb;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(S.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+
+    // last block: totals over the G partial slots
+    const int G = gridDim.x;
+    __shared__ float s_Z;
     if (warp == 0) {
-        z = warp_sum_f(s_f[lane]);
-        if (lane == 0) s_f[0] = z;
+        float zz = 0.f;
+        for (int b = lane; b < G; b += 32) zz += __ldcg(S.part + (size_t)b * (TN + 1) + TN);
+        zz = warp_sum_f(zz);
+        if (lane == 0) s_Z = zz;
     }
     __syncthreads();
-    const float Z = s_f[0];
-    const float invZ = 1.f / Z;
+    const float invZ = 1.f / s_Z;
+    for (int e = tid; e < TN; e += kUpdBlock) {
+        float tot = 0.f;
+        for (int b = 0; b < G; ++b) tot += __ldcg(S.part + (size_t)b * (TN + 1) + e);
+        const float v = U[e] + tot * invZ;
+        s_U[e] = v;
+        S.U_upd[e] = v;
+        if (U_upd_out) U_upd_out[e] = v;
+    }
     if (weights || costs) {
         for (int r = tid; r < K; r += kUpdBlock) {
-            if (weights) weights[r] = S.wt[r] * invZ;
+            if (weights) weights[r] = __ldcg(S.wt + r) * invZ;
             if (costs) costs[r] = (float)(S.J[r] + (double)P.w_inf * (double)S.chi[r]);
         }
     }
-
-    // U_h += sum_r omega_r eps'_{r,h}: thread -> (element e, sample slice)
-    const int slices = kUpdBlock / TN;
-    const int e = tid % TN, sl = tid / TN;
-    float acc = 0.f;
-    if (sl < slices) {
-        const float ue = U[e];
-        const int j = e % nu;
-        for (int r = sl; r < K; r += slices) {
-            const float eps = noise[(size_t)r * TN + e];
-            const float ep = P.clamp ? clamp_u(P, j, ue + eps) - ue : eps;
-            acc = fmaf(S.wt[r], ep, acc);
-        }
-    }
-    s_part[tid] = acc;
     __syncthreads();
-    if (tid < TN) {
-        float tot = 0.f;
-        for (int q = 0; q < slices; ++q) tot += s_part[q * TN + tid];
-        const float v = U[tid] + tot * invZ;
-        s_U[tid] = v;
-        S.U_upd[tid] = v;
-        if (U_upd_out) U_upd_out[tid] = v;
-    }
-    __syncthreads();
-
-    // rollout of the updated nominal (clamped like every sampled sequence)
     if (warp == 0) {
         LaneRollout R;
         warp_rollout(P, state[0], state[1], state[2], [&](int h, int j) { return clamp_u(P, j, s_U[h * nu + j]); }, R);
@@ -254,7 +300,8 @@ mppi_update_kernel(const MppiP P, const float *__restrict__ state, const float *
         }
         if (lane == 0) {
             *S.bad = 0;
-            *S.ticket = 0u;
+            S.ticket[0] = 0u;
+            S.ticket[1] = 0u;
         }
     }
 }
@@ -297,7 +344,7 @@ mppi_validate_kernel(const MppiP P, const FPC fpc, const float2 *__restrict__ pt
         const float d = b == finf() ? finf() : key_to_dist(fpc, b);
         if (!(d >= P.d_safe)) atomicExch(S.bad, 1);
         __threadfence();
-        const unsigned t = atomicAdd(S.ticket, 1u);
+        const unsigned t = atomicAdd(S.ticket + 1, 1u);
         s_last = (t == gridDim.x - 1);
     }
     __syncthreads();
@@ -313,7 +360,7 @@ mppi_validate_kernel(const MppiP P, const FPC fpc, const float2 *__restrict__ pt
     }
     if (threadIdx.x == 0) {
         if (valid_out) *valid_out = ok;
-        *S.ticket = 0u;
+        S.ticket[1] = 0u;
     }
 }
 
@@ -371,11 +418,12 @@ extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud,
     const int npairs = (n_points + 1) / 2;
     const int chunk_pairs = 1024;
     const int chunks = npairs > chunk_pairs ? (npairs + chunk_pairs - 1) / chunk_pairs : 1;
+    const size_t smem = (size_t)min(n_points, kStage) * sizeof(float2);
     return with_footprint(fp, [&](auto fpc) -> int {
         using FPC = decltype(fpc);
-        auto ka = mask ? mppi_sample_kernel<FPC, true> : mppi_sample_kernel<FPC, false>;
-        ka<<<P.K, kBlock, 0, st>>>(P, fpc, state, pts, mask, n_points, waypoints, n_wp, U, noise, S.J, S.chi, dmin);
-        mppi_update_kernel<<<1, kUpdBlock, 0, st>>>(P, state, U, noise, S, costs, weights, U_upd);
+        mppi_sample_kernel<FPC><<<P.K, kBlock, smem, st>>>(P, fpc, state, pts, mask, n_points, waypoints, n_wp, U,
+                                                            noise, S.J, S.chi, dmin);
+        mppi_update_kernel<<<upd_blocks(P.K), kUpdBlock, 0, st>>>(P, state, U, noise, S, costs, weights, U_upd);
         mppi_validate_kernel<FPC><<<P.T * chunks, kBlock, 0, st>>>(P, fpc, pts, mask, n_points, chunks,
                                                                    chunk_pairs, S, U, u_star, valid);
         return cuda_status(cudaGetLastError());
