@@ -40,6 +40,16 @@ size_t mppi_scratch_bytes(int K, int T);
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// The first kArenaHeader bytes of a context arena hold the MPPI cycle's
+// control words at fixed offsets (they must survive calls of other shapes
+// and other entry points); per-call arrays start after them.
+constexpr size_t kArenaHeader = 256;
+struct ArenaHeader {
+    unsigned long long beta_enc;   // ~order(J~) of the best sample, via atomicMax; 0 = empty
+    unsigned ticket[2];            // finished update / validation blocks
+    int bad;                       // validation failed
+};
+
 template <int E>
 inline PolyC<E> make_poly(const exact_footprint *fp) {
     PolyC<E> P;

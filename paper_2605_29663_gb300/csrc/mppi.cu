@@ -23,47 +23,58 @@
 
 namespace exact {
 
-constexpr int kUpdChunk = 128;    // samples per update block
 constexpr int kUpdBlock = 256;
+constexpr int kUpdTile = 8192;    // floats of noise one update block stages (32 KB)
 constexpr int kStage = 4096;      // obstacle points staged in shared memory per pass
 
 struct MppiScratch {
-    double *J;          // K
-    int *chi;           // K
+    ArenaHeader *hdr;   // beta, tickets, validation flag (fixed offset)
+    double *Jt;         // K   J~ = J + w_inf I(chi)
     float *wt;          // K   unnormalised weights exp(-(J~ - beta)/lambda)
     float *part;        // G x (T*nu + 1)   per-block weighted noise sums and Z
     float *U_upd;       // T x nu
     float4 *nom_pose;   // T   scored nominal states (x, y, cos, sin)
-    int *bad;           // 1   validation failed
-    unsigned *ticket;   // 2   finished update / validation blocks
 };
 
-static int upd_blocks(int K) { return (K + kUpdChunk - 1) / kUpdChunk; }
+// samples per update block: the block's noise tile fits kUpdTile floats
+static int upd_chunk(int T, int nu) {
+    const int c = kUpdTile / (T * nu);
+    return c < 1 ? 1 : (c > 256 ? 256 : c);
+}
+static int upd_blocks(int K, int T, int nu) {
+    const int c = upd_chunk(T, nu);
+    return (K + c - 1) / c;
+}
 
 size_t mppi_scratch_bytes(int K, int T) {
-    size_t b = 0;
+    size_t b = kArenaHeader;
     b += align_up((size_t)K * sizeof(double), 256);
-    b += align_up((size_t)K * sizeof(int), 256);
     b += align_up((size_t)K * sizeof(float), 256);
-    b += align_up((size_t)upd_blocks(K) * (T * 3 + 1) * sizeof(float), 256);
+    b += align_up((size_t)upd_blocks(K, T, 3) * (T * 3 + 1) * sizeof(float), 256);   // G is largest for n_u = 3
     b += align_up((size_t)T * 3 * sizeof(float), 256);
     b += align_up((size_t)T * sizeof(float4), 256);
-    b += 256 + 256;
     return b;
 }
 
 static MppiScratch carve(void *base, int K, int T) {
     char *p = static_cast<char *>(base);
     MppiScratch s;
-    s.J = reinterpret_cast<double *>(p); p += align_up((size_t)K * sizeof(double), 256);
-    s.chi = reinterpret_cast<int *>(p); p += align_up((size_t)K * sizeof(int), 256);
+    s.hdr = reinterpret_cast<ArenaHeader *>(p); p += kArenaHeader;
+    s.Jt = reinterpret_cast<double *>(p); p += align_up((size_t)K * sizeof(double), 256);
     s.wt = reinterpret_cast<float *>(p); p += align_up((size_t)K * sizeof(float), 256);
-    s.part = reinterpret_cast<float *>(p); p += align_up((size_t)upd_blocks(K) * (T * 3 + 1) * sizeof(float), 256);
+    s.part = reinterpret_cast<float *>(p); p += align_up((size_t)upd_blocks(K, T, 3) * (T * 3 + 1) * sizeof(float), 256);
     s.U_upd = reinterpret_cast<float *>(p); p += align_up((size_t)T * 3 * sizeof(float), 256);
-    s.nom_pose = reinterpret_cast<float4 *>(p); p += align_up((size_t)T * sizeof(float4), 256);
-    s.bad = reinterpret_cast<int *>(p); p += 256;
-    s.ticket = reinterpret_cast<unsigned *>(p);
+    s.nom_pose = reinterpret_cast<float4 *>(p);
     return s;
+}
+
+// Order-preserving map of a double onto uint64 (total order).
+__device__ __forceinline__ unsigned long long d2ord(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord2d(unsigned long long u) {
+    return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
 }
 
 constexpr int kPairsPerLane = 4;   // point pairs one lane evaluates per work item
@@ -127,8 +138,8 @@ __global__ void __launch_bounds__(kBlock)
 mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state,
                    const float2 *__restrict__ pts, const uint8_t *__restrict__ mask, int N,
                    const float *__restrict__ wp, int W, const float *__restrict__ U,
-                   const float *__restrict__ noise, double *__restrict__ Jout, int *__restrict__ chi_out,
-                   float *__restrict__ dmin_out) {
+                   const float *__restrict__ noise, double *__restrict__ Jt_out, float *__restrict__ dmin_out,
+                   ArenaHeader *__restrict__ hdr) {
     extern __shared__ float2 s_pts[];            // min(N, kStage) staged points
     __shared__ float4 s_pose[EXACT_MAX_HORIZON];
     __shared__ float s_stage[EXACT_MAX_HORIZON];
@@ -137,6 +148,13 @@ mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state
     const int r = blockIdx.x;
     const int T = P.T, nu = P.nu;
     for (int h = threadIdx.x; h < T; h += blockDim.x) s_key[h] = f2ord(finf());
+    if (r == 0 && threadIdx.x == 0) {
+        // the update and validation kernels that follow on the stream count
+        // finished blocks on these tickets; start them from zero every cycle
+        hdr->ticket[0] = 0u;
+        hdr->ticket[1] = 0u;
+        hdr->bad = 0;
+    }
 
     const int n0 = min(N, kStage);
     if (threadIdx.x < 32) {
@@ -184,48 +202,50 @@ mppi_sample_kernel(const MppiP P, const FPC fpc, const float *__restrict__ state
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         const bool chi = __any_sync(0xffffffffu, unsafe);
         if (threadIdx.x == 0) {
-            Jout[r] = acc + (double)s_term;
-            chi_out[r] = chi ? 1 : 0;
+            // J~ = J + w_inf I(chi) in double (Sec. IV-E); beta = min J~ is
+            // gathered with one 64-bit atomic per sample (the arena header
+            // holds its complement, reset to 0 when the cycle ends)
+            const double jt = acc + (double)s_term + (chi ? (double)P.w_inf : 0.0);
+            Jt_out[r] = jt;
+            atomicMax(&hdr->beta_enc, ~d2ord(jt));
         }
     }
 }
 
-// B1: block b owns samples [b * kUpdChunk, (b + 1) * kUpdChunk).  Every block
-// reduces beta = min_r J~_r over all K itself (J~ = J + w_inf I(chi) in
-// double, so the large offset costs no precision), forms the unnormalised
-// weights of its samples and their weighted clipped perturbations, and
-// leaves (sum w eps', sum w) in its partial slot.  The last block to finish
-// (atomic ticket) adds the partials, writes the normalised weights, costs
-// and U_upd, and rolls the updated nominal out for validation.
+// B1: block b owns `chunk` consecutive samples, sized so that their noise
+// rows (chunk x T x n_u floats, contiguous) fit one shared-memory tile that
+// the block loads with coalesced reads.  It forms the unnormalised weights
+// w_r = exp(-(J~_r - beta)/lambda) of its samples and the sums
+// sum_r w_r eps'_r and sum_r w_r, left in its partial slot.  The last block
+// to finish (atomic ticket) adds the partials, writes the normalised
+// weights, costs and U_upd, and rolls the updated nominal out.
 __global__ void __launch_bounds__(kUpdBlock)
-mppi_update_kernel(const MppiP P, const float *__restrict__ state, const float *__restrict__ U,
+mppi_update_kernel(const MppiP P, int chunk, const float *__restrict__ state, const float *__restrict__ U,
                    const float *__restrict__ noise, MppiScratch S, float *__restrict__ costs,
                    float *__restrict__ weights, float *__restrict__ U_upd_out) {
-    __shared__ double s_J[kUpdBlock / 32];
-    __shared__ float s_w[kUpdChunk];
+    __shared__ float s_tile[kUpdTile];
+    __shared__ float s_w[256];
     __shared__ float s_f[kUpdBlock / 32];
     __shared__ float s_U[EXACT_MAX_HORIZON * 3];
     __shared__ bool s_last;
+    __shared__ float s_Z;
     const int K = P.K, T = P.T, nu = P.nu, TN = T * nu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int r0 = blockIdx.x * kUpdChunk, r1 = min(K, r0 + kUpdChunk);
+    const int r0 = blockIdx.x * chunk, r1 = min(K, r0 + chunk), nr = r1 - r0;
+    const double beta = ord2d(~S.hdr->beta_enc);
 
-    double bJ = __longlong_as_double(0x7ff0000000000000ll);
-    for (int r = tid; r < K; r += kUpdBlock) bJ = fmin(bJ, S.J[r] + (double)P.w_inf * (double)S.chi[r]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bJ = fmin(bJ, __shfl_xor_sync(0xffffffffu, bJ, o));
-    if (lane == 0) s_J[warp] = bJ;
-    __syncthreads();
-    double beta = s_J[0];
-#pragma unroll
-    for (int w = 1; w < kUpdBlock / 32; ++w) beta = fmin(beta, s_J[w]);
-
+    // stage the noise rows of this block's samples (clipped perturbations)
+    const float *src = noise + (size_t)r0 * TN;
+    for (int i = tid; i < nr * TN; i += kUpdBlock) {
+        const int e = i % TN;
+        const float eps = __ldg(src + i);
+        s_tile[i] = P.clamp ? clamp_u(P, e % nu, U[e] + eps) - U[e] : eps;
+    }
     float z = 0.f;
-    for (int r = r0 + tid; r < r1; r += kUpdBlock) {
-        const double diff = (S.J[r] + (double)P.w_inf * (double)S.chi[r]) - beta;
-        const float w = expf(-(float)diff / P.lambda);
-        s_w[r - r0] = w;
-        S.wt[r] = w;
+    for (int i = tid; i < nr; i += kUpdBlock) {
+        const float w = expf(-(float)(S.Jt[r0 + i] - beta) / P.lambda);
+        s_w[i] = w;
+        S.wt[r0 + i] = w;
         z += w;
     }
     z = warp_sum_f(z);
@@ -233,19 +253,13 @@ mppi_update_kernel(const MppiP P, const float *__restrict__ state, const float *
     __syncthreads();
     float *part = S.part + (size_t)blockIdx.x * (TN + 1);
     for (int e = tid; e < TN; e += kUpdBlock) {
-        const float ue = U[e];
-        const int j = e % nu;
         float a0 = 0.f, a1 = 0.f;
-        int r = r0;
-        for (; r + 1 < r1; r += 2) {
-            const float e0 = noise[(size_t)r * TN + e], e1 = noise[(size_t)(r + 1) * TN + e];
-            a0 = fmaf(s_w[r - r0], P.clamp ? clamp_u(P, j, ue + e0) - ue : e0, a0);
-            a1 = fmaf(s_w[r + 1 - r0], P.clamp ? clamp_u(P, j, ue + e1) - ue : e1, a1);
+        int i = 0;
+        for (; i + 1 < nr; i += 2) {
+            a0 = fmaf(s_w[i], s_tile[i * TN + e], a0);
+            a1 = fmaf(s_w[i + 1], s_tile[(i + 1) * TN + e], a1);
         }
-        if (r < r1) {
-            const float e0 = noise[(size_t)r * TN + e];
-            a0 = fmaf(s_w[r - r0], P.clamp ? clamp_u(P, j, ue + e0) - ue : e0, a0);
-        }
+        if (i < nr) a0 = fmaf(s_w[i], s_tile[i * TN + e], a0);
         part[e] = a0 + a1;
     }
     if (tid == 0) {
@@ -255,14 +269,13 @@ mppi_update_kernel(const MppiP P, const float *__restrict__ state, const float *
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(S.ticket, 1u) == gridDim.x - 1;
+    if (tid == 0) s_last = atomicAdd(&S.hdr->ticket[0], 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
 
-    // last block: totals over the G partial slots
+    // last block: totals over the G partial slots (four independent sums per thread)
     const int G = gridDim.x;
-    __shared__ float s_Z;
     if (warp == 0) {
         float zz = 0.f;
         for (int b = lane; b < G; b += 32) zz += __ldcg(S.part + (size_t)b * (TN + 1) + TN);
@@ -272,9 +285,16 @@ mppi_update_kernel(const MppiP P, const float *__restrict__ state, const float *
     __syncthreads();
     const float invZ = 1.f / s_Z;
     for (int e = tid; e < TN; e += kUpdBlock) {
-        float tot = 0.f;
-        for (int b = 0; b < G; ++b) tot += __ldcg(S.part + (size_t)b * (TN + 1) + e);
-        const float v = U[e] + tot * invZ;
+        float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+        int b = 0;
+        for (; b + 3 < G; b += 4) {
+            t0 += __ldcg(S.part + (size_t)b * (TN + 1) + e);
+            t1 += __ldcg(S.part + (size_t)(b + 1) * (TN + 1) + e);
+            t2 += __ldcg(S.part + (size_t)(b + 2) * (TN + 1) + e);
+            t3 += __ldcg(S.part + (size_t)(b + 3) * (TN + 1) + e);
+        }
+        for (; b < G; ++b) t0 += __ldcg(S.part + (size_t)b * (TN + 1) + e);
+        const float v = U[e] + ((t0 + t1) + (t2 + t3)) * invZ;
         s_U[e] = v;
         S.U_upd[e] = v;
         if (U_upd_out) U_upd_out[e] = v;
@@ -282,7 +302,7 @@ mppi_update_kernel(const MppiP P, const float *__restrict__ state, const float *
     if (weights || costs) {
         for (int r = tid; r < K; r += kUpdBlock) {
             if (weights) weights[r] = __ldcg(S.wt + r) * invZ;
-            if (costs) costs[r] = (float)(S.J[r] + (double)P.w_inf * (double)S.chi[r]);
+            if (costs) costs[r] = (float)S.Jt[r];
         }
     }
     __syncthreads();
@@ -297,11 +317,6 @@ mppi_update_kernel(const MppiP P, const float *__restrict__ state, const float *
                 sincosf(R.th[q], &sn, &cs);
                 S.nom_pose[h] = make_float4(R.x[q], R.y[q], cs, sn);
             }
-        }
-        if (lane == 0) {
-            *S.bad = 0;
-            S.ticket[0] = 0u;
-            S.ticket[1] = 0u;
         }
     }
 }
@@ -342,15 +357,15 @@ mppi_validate_kernel(const MppiP P, const FPC fpc, const float2 *__restrict__ pt
         float b = s_min[0];
         for (int w = 1; w < kBlock / 32; ++w) b = fminf(b, s_min[w]);
         const float d = b == finf() ? finf() : key_to_dist(fpc, b);
-        if (!(d >= P.d_safe)) atomicExch(S.bad, 1);
+        if (!(d >= P.d_safe)) atomicExch(&S.hdr->bad, 1);
         __threadfence();
-        const unsigned t = atomicAdd(S.ticket + 1, 1u);
+        const unsigned t = atomicAdd(&S.hdr->ticket[1], 1u);
         s_last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const int ok = atomicAdd(S.bad, 0) == 0;
+    const int ok = atomicAdd(&S.hdr->bad, 0) == 0;
     const int T = P.T, nu = P.nu, TN = T * nu;
     for (int e = threadIdx.x; e < TN; e += kBlock) {
         const float v = S.U_upd[e];
@@ -360,7 +375,7 @@ mppi_validate_kernel(const MppiP P, const FPC fpc, const float2 *__restrict__ pt
     }
     if (threadIdx.x == 0) {
         if (valid_out) *valid_out = ok;
-        S.ticket[1] = 0u;
+        S.hdr->beta_enc = 0ull;   // empty for the next cycle's atomicMax
     }
 }
 
@@ -422,8 +437,9 @@ extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud,
     return with_footprint(fp, [&](auto fpc) -> int {
         using FPC = decltype(fpc);
         mppi_sample_kernel<FPC><<<P.K, kBlock, smem, st>>>(P, fpc, state, pts, mask, n_points, waypoints, n_wp, U,
-                                                            noise, S.J, S.chi, dmin);
-        mppi_update_kernel<<<upd_blocks(P.K), kUpdBlock, 0, st>>>(P, state, U, noise, S, costs, weights, U_upd);
+                                                            noise, S.Jt, dmin, S.hdr);
+        mppi_update_kernel<<<upd_blocks(P.K, P.T, P.nu), kUpdBlock, 0, st>>>(P, upd_chunk(P.T, P.nu), state, U,
+                                                                             noise, S, costs, weights, U_upd);
         mppi_validate_kernel<FPC><<<P.T * chunks, kBlock, 0, st>>>(P, fpc, pts, mask, n_points, chunks,
                                                                    chunk_pairs, S, U, u_star, valid);
         return cuda_status(cudaGetLastError());

@@ -98,7 +98,7 @@ __global__ void sdf_keys_finish(const unsigned long long *__restrict__ keys, int
     if (argmin) argmin[p] = b == kNoKey ? -1 : (int)(unsigned)(b & 0xffffffffu);
 }
 
-size_t sdf_scratch_bytes(int n_poses) { return align_up((size_t)n_poses * sizeof(unsigned long long), 256); }
+size_t sdf_scratch_bytes(int n_poses) { return kArenaHeader + align_up((size_t)n_poses * sizeof(unsigned long long), 256); }
 
 }  // namespace exact
 
@@ -134,7 +134,7 @@ extern "C" int exact_sdf_batch(exact_ctx *ctx, const float *points, const uint8_
     if (chunks > 1 && (dmin || argmin)) {
         const int rc = ensure_scratch(ctx, sdf_scratch_bytes(n_poses));
         if (rc != EXACT_OK) return rc;
-        keys = reinterpret_cast<unsigned long long *>(ctx->scratch);
+        keys = reinterpret_cast<unsigned long long *>(static_cast<char *>(ctx->scratch) + kArenaHeader);
         sdf_keys_init<<<(n_poses + 255) / 256, 256, 0, st>>>(keys, n_poses);
     }
     const float2 *p2 = reinterpret_cast<const float2 *>(points);

@@ -212,3 +212,23 @@ def test_full_size_forklift_sampled(ex, ctx):
     upd = U0 + np.einsum("r,rtj->tj", g["weights"].astype(np.float64), epsc)
     scale = np.maximum(np.abs(upd), np.array([0.3, 0.2]))
     assert np.max(np.abs(g["U_upd"] - upd) / scale) <= REL
+
+
+def test_context_reused_across_shapes_and_entry_points(ex):
+    """One context serves cycles of different (K, T), interleaved with
+    exact_sdf_batch calls that use the same arena, and gives the same result
+    as a fresh context each time."""
+    import torch
+    shared = ex.Context()
+    for k, (K, T, N) in enumerate([(300, 9, 200), (64, 30, 129), (1024, 5, 700), (300, 9, 200)]):
+        s = synth.plain_step(60 + k, K=K, T=T, N=N)
+        g1 = run_gpu(ex, shared, s)
+        g2 = run_gpu(ex, ex.Context(), s)
+        for key in ("weights", "U_upd", "U", "u_star", "costs", "dmin"):
+            np.testing.assert_array_equal(g1[key], g2[key], err_msg=key)
+        assert g1["valid"] == g2["valid"]
+        # an SDF batch whose points spread over several blocks uses the arena too
+        pts = torch.from_numpy(synth.uniform_points(synth.rng(k), 40001, -5, 5)).cuda()
+        ex.sdf_batch(pts, torch.zeros((2, 3), device="cuda"), ex.Footprint(s["kind"], s["fp"]), ctx=shared,
+                     dist=False)
+        torch.cuda.synchronize()
