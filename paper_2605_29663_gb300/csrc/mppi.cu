@@ -116,13 +116,24 @@ __device__ __forceinline__ void steps_min_keys(const FPC &fpc, const float2 *pts
 }
 
 // Copy points [base, base + n) into shared memory, masked ones as NaN.
+// Eight loads per thread are in flight before the first store.
 __device__ __forceinline__ void stage_points(float2 *dst, const float2 *__restrict__ pts,
                                              const uint8_t *__restrict__ mask, int base, int n, int t0, int nt) {
     const float qnan = __int_as_float(0x7fffffff);
-    for (int i = t0; i < n; i += nt) {
-        float2 p = __ldg(pts + base + i);
-        if (mask && !__ldg(mask + base + i)) p = make_float2(qnan, qnan);
-        dst[i] = p;
+    for (int i0 = t0; i0 < n; i0 += 8 * nt) {
+        float2 p[8];
+        bool ok[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k * nt;
+            p[k] = i < n ? __ldg(pts + base + i) : make_float2(0.f, 0.f);
+            ok[k] = i < n && (!mask || __ldg(mask + base + i));
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k * nt;
+            if (i < n) dst[i] = ok[k] ? p[k] : make_float2(qnan, qnan);
+        }
     }
 }
 
@@ -234,12 +245,25 @@ mppi_update_kernel(const MppiP P, int chunk, const float *__restrict__ state, co
     const int r0 = blockIdx.x * chunk, r1 = min(K, r0 + chunk), nr = r1 - r0;
     const double beta = ord2d(~S.hdr->beta_enc);
 
-    // stage the noise rows of this block's samples (clipped perturbations)
+    // stage the noise rows of this block's samples (clipped perturbations),
+    // eight loads per thread in flight
     const float *src = noise + (size_t)r0 * TN;
-    for (int i = tid; i < nr * TN; i += kUpdBlock) {
-        const int e = i % TN;
-        const float eps = __ldg(src + i);
-        s_tile[i] = P.clamp ? clamp_u(P, e % nu, U[e] + eps) - U[e] : eps;
+    const int n = nr * TN;
+    for (int i0 = tid; i0 < n; i0 += 8 * kUpdBlock) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k * kUpdBlock;
+            v[k] = i < n ? __ldg(src + i) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k * kUpdBlock;
+            if (i < n) {
+                const int e = i % TN;
+                s_tile[i] = P.clamp ? clamp_u(P, e % nu, U[e] + v[k]) - U[e] : v[k];
+            }
+        }
     }
     float z = 0.f;
     for (int i = tid; i < nr; i += kUpdBlock) {
