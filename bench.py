@@ -226,6 +226,56 @@ def mppi_extra(torch, ex, dev):
     return out
 
 
+def batched_extra(torch, ex, dev, steps=3, tune=True):
+    """The 64-scene heterogeneous batch: one persistent launch per step vs the
+    same scenes as 64 consecutive single-scene mppi_step calls."""
+    import synth
+    scenes = synth.batched(0)
+    devs = []
+    for s in scenes:
+        devs.append(dict(state=torch.from_numpy(s["q0"]).to(dev), cloud=torch.from_numpy(s["cloud"]).to(dev),
+                         waypoints=torch.from_numpy(s["waypoints"]).to(dev), U=torch.from_numpy(s["U"]).to(dev),
+                         noise=torch.from_numpy(s["eps"]).to(dev),
+                         mask=None if s["mask"] is None else torch.from_numpy(s["mask"]).to(dev),
+                         fp=ex.Footprint(s["kind"], s["fp"]), params=s["params"]))
+    evals = sum(s["params"]["K"] * s["params"]["T"] * s["cloud"].shape[0] * s["fp"].shape[0] for s in scenes)
+    b = ex.Batch(devs)
+    report = b.autotune(iters=1) if tune else None
+    b.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        b.step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / steps
+    ctx = ex.Context()
+    ctx.reserve(0, max(s["params"]["K"] for s in scenes), max(s["params"]["T"] for s in scenes))
+    outs = [dict() for _ in devs]
+
+    def singles():
+        for d, o in zip(devs, outs):
+            o.update(ex.mppi_step(ctx, d["state"], d["cloud"], d["waypoints"], d["U"], d["noise"], d["fp"],
+                                  d["params"], mask=d["mask"], out=o))
+
+    singles()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        singles()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1) / steps
+    return {"scenes": len(scenes), "point_edge_evals_per_step": evals,
+            "batched_ms_per_step": ms_b, "batched_scene_steps_per_s": len(scenes) * 1e3 / ms_b,
+            "batched_counted_tflops": FLOPS_PER_POINT_EDGE * evals / (ms_b * 1e-3) / 1e12,
+            "single_launches_ms_per_step": ms_s, "single_scene_steps_per_s": len(scenes) * 1e3 / ms_s,
+            "speedup_vs_single_launches": ms_s / ms_b, "tiles": list(b.tiles),
+            "autotune": report, "launches_per_step": 3,
+            "timing": "events over consecutive steps (no graph); same scenes, same GPU"}
+
+
 def run_mppi_workload(args):
     """Time one MPPI cycle workload (plain_step or forklift) as plain launches."""
     import torch
@@ -390,6 +440,7 @@ def run_gpu(args):
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if not args.no_extra:
         line["extra"] = mppi_extra(torch, ex, dev)
+        line["extra"]["batched64"] = batched_extra(torch, ex, dev)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

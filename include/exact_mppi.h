@@ -153,6 +153,61 @@ int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint
               float *u_star, float *costs, float *weights, int *valid, float *U_upd,
               float *dmin, void *stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent scenes (robots) with different K, T, N, footprints and
+ * motion models advanced by one control cycle each in a single persistent
+ * launch (plus two small table-driven launches for the update and the
+ * validation).  A scene is Algorithm 1 exactly as in mppi_step; only the
+ * scheduling differs.  Every pointer in exact_scene refers to caller-owned
+ * device memory laid out as for mppi_step (optional outputs may be NULL);
+ * fp is a footprint object (its constants are copied into the batch). */
+typedef struct {
+    const float *state;          /* device, 3 */
+    const float *cloud;          /* device, n_points x 2 */
+    const uint8_t *mask;         /* device, n_points, or NULL */
+    int n_points;
+    const float *waypoints;      /* device, n_wp x 2 */
+    int n_wp;
+    float *U;                    /* device, T x n_u, in/out */
+    const float *noise;          /* device, K x T x n_u */
+    const exact_footprint *fp;
+    exact_mppi_params params;
+    float *u_star;               /* device, n_u */
+    float *costs;                /* device, K, or NULL */
+    float *weights;              /* device, K, or NULL */
+    int *valid;                  /* device, 1, or NULL */
+    float *U_upd;                /* device, T x n_u, or NULL */
+    float *dmin;                 /* device, K x T, or NULL */
+} exact_scene;
+
+/* A batch plan: validates the scenes, uploads a device scene table, the
+ * work-item list (one item per (scene, sample), heaviest first) and the
+ * per-scene scratch (synchronous; allocates device memory).  The scene
+ * pointers are fixed for the life of the plan; their contents may change
+ * between steps.  1 <= n_scenes <= 4096; each scene obeys the mppi_step
+ * limits.  *out is released with exact_batch_destroy. */
+typedef struct exact_batch exact_batch;
+int exact_batch_create(int n_scenes, const exact_scene *scenes, exact_batch **out);
+void exact_batch_destroy(exact_batch *batch);
+
+/* One control cycle of every scene of the batch: a queue reset, the
+ * persistent sample kernel, the update kernel and the validation kernel on
+ * `stream` (no allocation, no host synchronisation: capturable in a CUDA
+ * graph).  Calls on one batch must not overlap on the GPU. */
+int mppi_step_batched(exact_batch *batch, void *stream);
+
+/* Tile autotuner: times the batch's sample phase (which writes only batch
+ * scratch, never the scenes' U or outputs) for each candidate tile shape
+ * (threads per block x point pairs per lane per work item), `iters` runs
+ * each, keeps the fastest for later steps and, when json_out is non-NULL,
+ * writes the timings as JSON text (at most json_cap bytes, NUL-terminated).
+ * Synchronises `stream`. */
+int exact_batch_autotune(exact_batch *batch, int iters, char *json_out, int json_cap, void *stream);
+/* Current tile shape of the batch. */
+int exact_batch_get_tiles(const exact_batch *batch, int *threads, int *pairs_per_lane);
+/* Set the tile shape (threads in {64, 128, 256, 512}, pairs_per_lane in 1..8). */
+int exact_batch_set_tiles(exact_batch *batch, int threads, int pairs_per_lane);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,7 @@ import threading
 
 from . import build as _build
 
-__all__ = ["load", "Footprint", "Context", "MppiParams", "sdf_batch", "mppi_step", "ExactError",
+__all__ = ["load", "Footprint", "Context", "MppiParams", "sdf_batch", "mppi_step", "Batch", "ExactError",
            "POLYGON", "RECTS", "DIFF", "ACKERMANN", "OMNI", "SPIN", "PARALLEL", "NU", "EXPORTS"]
 
 POLYGON, RECTS = 0, 1
@@ -25,7 +25,8 @@ NU = {DIFF: 2, ACKERMANN: 2, OMNI: 3, SPIN: 1, PARALLEL: 1}
 # every symbol declared in include/exact_mppi.h
 EXPORTS = ["exact_status_string", "exact_footprint_create", "exact_footprint_destroy",
            "exact_footprint_info", "exact_ctx_create", "exact_ctx_destroy", "exact_ctx_reserve",
-           "exact_ctx_get_error", "exact_sdf_batch", "mppi_step"]
+           "exact_ctx_get_error", "exact_sdf_batch", "mppi_step", "exact_batch_create", "exact_batch_destroy",
+           "mppi_step_batched", "exact_batch_autotune", "exact_batch_get_tiles", "exact_batch_set_tiles"]
 
 _lock = threading.Lock()
 _lib = None
@@ -68,6 +69,18 @@ def load() -> ctypes.CDLL:
         lib.exact_sdf_batch.argtypes = [P, P, P, I, P, I, P, P, P, P, P]
         lib.mppi_step.restype = I
         lib.mppi_step.argtypes = [P, P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
+        lib.exact_batch_create.restype = I
+        lib.exact_batch_create.argtypes = [I, P, ctypes.POINTER(P)]
+        lib.exact_batch_destroy.restype = V
+        lib.exact_batch_destroy.argtypes = [P]
+        lib.mppi_step_batched.restype = I
+        lib.mppi_step_batched.argtypes = [P, P]
+        lib.exact_batch_autotune.restype = I
+        lib.exact_batch_autotune.argtypes = [P, I, ctypes.c_char_p, I, P]
+        lib.exact_batch_get_tiles.restype = I
+        lib.exact_batch_get_tiles.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+        lib.exact_batch_set_tiles.restype = I
+        lib.exact_batch_set_tiles.argtypes = [P, I, I]
         _lib = lib
         return lib
 
@@ -273,3 +286,99 @@ def mppi_step(ctx: Context, state, cloud, waypoints, U, noise, footprint: Footpr
                             _ptr(o["u_star"]), _ptr(o.get("costs")), _ptr(o.get("weights")), _ptr(o["valid"]),
                             _ptr(o.get("U_upd")), _ptr(o.get("dmin")), _stream(stream)), "mppi_step")
     return o
+
+
+class ExactScene(ctypes.Structure):
+    """Mirror of exact_scene."""
+    _fields_ = [("state", ctypes.c_void_p), ("cloud", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("n_points", ctypes.c_int), ("waypoints", ctypes.c_void_p), ("n_wp", ctypes.c_int),
+                ("U", ctypes.c_void_p), ("noise", ctypes.c_void_p), ("fp", ctypes.c_void_p),
+                ("params", MppiParams), ("u_star", ctypes.c_void_p), ("costs", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("valid", ctypes.c_void_p), ("U_upd", ctypes.c_void_p),
+                ("dmin", ctypes.c_void_p)]
+
+
+class Batch:
+    """Plan + device scratch for advancing many scenes by one control cycle
+    each in one persistent launch (mppi_step_batched).
+
+    `scenes` is a list of dicts with device tensors state, cloud, waypoints,
+    U (in/out), noise, optional mask, a Footprint `fp` and `params`.  Output
+    tensors (u_star, valid, costs, weights, U_upd, and dmin when
+    dmin=True) are allocated here and exposed as `outputs[i]`."""
+
+    def __init__(self, scenes, *, dmin=False, costs=True, weights=True, U_upd=True):
+        torch = _torch()
+        self._keep = []
+        arr = (ExactScene * len(scenes))()
+        self.outputs = []
+        for i, sc in enumerate(scenes):
+            p = sc["params"] if isinstance(sc["params"], MppiParams) else MppiParams.from_dict(sc["params"])
+            K, T, nu = p.K, p.T, p.n_u
+            state = _dev(sc["state"], "state", torch.float32, (3,))
+            U = _dev(sc["U"], "U", torch.float32, (T, nu))
+            noise = _dev(sc["noise"], "noise", torch.float32, (K, T, nu))
+            wp = _dev(sc["waypoints"], "waypoints", torch.float32)
+            cloud = _dev(sc["cloud"], "cloud", torch.float32)
+            N = cloud.shape[0] if cloud.numel() else 0
+            mask = sc.get("mask")
+            if mask is not None:
+                mask = _dev(mask, "mask", torch.uint8, (N,))
+            dev = U.device
+            o = {"u_star": torch.empty(nu, dtype=torch.float32, device=dev),
+                 "valid": torch.empty(1, dtype=torch.int32, device=dev)}
+            if costs:
+                o["costs"] = torch.empty(K, dtype=torch.float32, device=dev)
+            if weights:
+                o["weights"] = torch.empty(K, dtype=torch.float32, device=dev)
+            if U_upd:
+                o["U_upd"] = torch.empty((T, nu), dtype=torch.float32, device=dev)
+            if dmin:
+                o["dmin"] = torch.empty((K, T), dtype=torch.float32, device=dev)
+            self.outputs.append(o)
+            self._keep += [state, U, noise, wp, cloud, mask, sc["fp"]]
+            e = arr[i]
+            e.state, e.cloud, e.mask, e.n_points = state.data_ptr(), cloud.data_ptr() if N else None, \
+                None if mask is None else mask.data_ptr(), N
+            e.waypoints, e.n_wp, e.U, e.noise = wp.data_ptr(), wp.shape[0], U.data_ptr(), noise.data_ptr()
+            e.fp = sc["fp"].handle
+            e.params = p
+            e.u_star, e.valid = o["u_star"].data_ptr(), o["valid"].data_ptr()
+            e.costs = o["costs"].data_ptr() if costs else None
+            e.weights = o["weights"].data_ptr() if weights else None
+            e.U_upd = o["U_upd"].data_ptr() if U_upd else None
+            e.dmin = o["dmin"].data_ptr() if dmin else None
+        h = ctypes.c_void_p()
+        _check(load().exact_batch_create(len(scenes), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(h)),
+               "exact_batch_create")
+        self._h = h
+        self.n = len(scenes)
+
+    def step(self, stream=None):
+        _check(load().mppi_step_batched(self._h, _stream(stream)), "mppi_step_batched")
+
+    def autotune(self, iters: int = 3, stream=None) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(8192)
+        _check(load().exact_batch_autotune(self._h, iters, buf, 8192, _stream(stream)), "exact_batch_autotune")
+        return json.loads(buf.value.decode())
+
+    @property
+    def tiles(self):
+        t, p = ctypes.c_int(), ctypes.c_int()
+        _check(load().exact_batch_get_tiles(self._h, ctypes.byref(t), ctypes.byref(p)), "exact_batch_get_tiles")
+        return t.value, p.value
+
+    def set_tiles(self, threads: int, pairs_per_lane: int):
+        _check(load().exact_batch_set_tiles(self._h, threads, pairs_per_lane), "exact_batch_set_tiles")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().exact_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,489 @@
+// mppi_cycle.cuh -- the three phases of one control cycle (Algorithm 1) as
+// block-level device bodies, shared by the single-scene kernels (mppi.cu)
+// and the batched persistent kernels (batched.cu):
+//   sample_body    one sample r: rollout, every (step, point) body-frame
+//                  signed distance, per-step minima, J~ (Sec. III-E, IV-C..E)
+//   update_body    one chunk of samples: weights and weighted clipped noise;
+//                  the scene's last chunk sums them, writes U_upd and rolls
+//                  the updated nominal out (Alg. 1 step 3)
+//   validate_body  one (step, point chunk) of the nominal: d_min >= d_safe;
+//                  the scene's last block writes u*, the shifted or reset U
+//                  and the valid flag (Alg. 1 step 4)
+// Blocks never wait for each other: the last block of a phase is found with
+// an atomic ticket.  A footprint is reached through an evaluator object that
+// provides eval2 (two points -> two order keys) and dist (key -> signed
+// distance), either with compile-time constants or from shared memory.
+#pragma once
+
+#include "internal.h"
+#include "mppi_common.cuh"
+
+namespace exact {
+
+constexpr int kUpdBlock = 256;
+constexpr int kUpdTile = 8192;    // floats of noise one update block stages (32 KB)
+constexpr int kStage = 4096;      // obstacle points staged in shared memory per pass
+constexpr int kValChunkPairs = 1024;
+
+// Everything the phases need about one scene.
+struct SceneView {
+    MppiP P;
+    const float *state;
+    const float2 *pts;
+    const uint8_t *mask;
+    int N;
+    const float *wp;
+    int W;
+    float *U;
+    const float *noise;
+    float *u_star, *costs, *weights, *U_upd_out, *dmin;
+    int *valid;
+    ArenaHeader *hdr;   // beta, tickets, validation flag
+    double *Jt;         // K   J~ = J + w_inf I(chi)
+    float *wt;          // K   unnormalised weights
+    float *part;        // G x (T*nu + 1) partial sums
+    float *Uupd;        // T x nu
+    float4 *nom;        // T   scored nominal states (x, y, cos, sin)
+    int upd_chunk, upd_blocks, val_chunks;
+};
+
+// samples per update block: the block's noise tile fits kUpdTile floats
+inline int upd_chunk_for(int T, int nu) {
+    const int c = kUpdTile / (T * nu);
+    return c < 1 ? 1 : (c > 256 ? 256 : c);
+}
+inline int upd_blocks_for(int K, int T, int nu) {
+    const int c = upd_chunk_for(T, nu);
+    return (K + c - 1) / c;
+}
+inline int val_chunks_for(int N) {
+    const int np = (N + 1) / 2;
+    return np > kValChunkPairs ? (np + kValChunkPairs - 1) / kValChunkPairs : 1;
+}
+
+// Per-scene arena bytes after the header (n_u = 3 bounds the update blocks).
+inline size_t scene_scratch_bytes(int K, int T) {
+    size_t b = 0;
+    b += align_up((size_t)K * sizeof(double), 256);
+    b += align_up((size_t)K * sizeof(float), 256);
+    b += align_up((size_t)upd_blocks_for(K, T, 3) * (T * 3 + 1) * sizeof(float), 256);
+    b += align_up((size_t)T * 3 * sizeof(float), 256);
+    b += align_up((size_t)T * sizeof(float4), 256);
+    return b;
+}
+inline void carve_scene(SceneView &V, char *p, int K, int T) {
+    V.Jt = reinterpret_cast<double *>(p); p += align_up((size_t)K * sizeof(double), 256);
+    V.wt = reinterpret_cast<float *>(p); p += align_up((size_t)K * sizeof(float), 256);
+    V.part = reinterpret_cast<float *>(p); p += align_up((size_t)upd_blocks_for(K, T, 3) * (T * 3 + 1) * sizeof(float), 256);
+    V.Uupd = reinterpret_cast<float *>(p); p += align_up((size_t)T * 3 * sizeof(float), 256);
+    V.nom = reinterpret_cast<float4 *>(p);
+}
+
+// Order-preserving map of a double onto uint64 (total order).
+__device__ __forceinline__ unsigned long long d2ord(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord2d(unsigned long long u) {
+    return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
+}
+
+// ---------------------------------------------------------------- evaluators
+template <class FPC>
+struct ConstEval {            // footprint constants in the kernel parameters
+    FPC f;
+    __device__ __forceinline__ void eval2(float px0, float py0, float px1, float py1, float &k0, float &k1) const {
+        exact::eval2(f, px0, py0, px1, py1, k0, k1);
+    }
+    __device__ __forceinline__ float dist(float key) const { return key_to_dist(f, key); }
+};
+
+// Footprint constants in shared memory with a run-time edge / box count.
+// Polygon: C[2b] = (v_bx, v_by, e_bx/|e_b|^2, e_by/|e_b|^2),
+// C[2b+1] = (e_bx, e_by, e_bx/e_by, 0) for b < E, and C[2E] = C[0] (the
+// closing vertex).  Rects: C[j] = (cx, cy, sx, sy).  The arithmetic is the
+// same sequence of operations as the compile-time evaluators, so both give
+// identical keys.
+struct SmemEval {
+    const float4 *C;
+    int kind, n;
+    __device__ __forceinline__ void eval2(float px0, float py0, float px1, float py1, float &k0, float &k1) const {
+        if (kind == EXACT_FP_POLYGON) {
+            float4 c = C[0];
+            float dxa0 = px0 - c.x, dya0 = py0 - c.y, dxa1 = px1 - c.x, dya1 = py1 - c.y;
+            float m0 = finf(), m1 = finf();
+            unsigned s0 = 0u, s1 = 0u;
+#pragma unroll 2
+            for (int b = 0; b < n; ++b) {
+                const float4 e = C[2 * b + 1];
+                const float4 nx = C[2 * b + 2];
+                const float dxb0 = px0 - nx.x, dyb0 = py0 - nx.y, dxb1 = px1 - nx.x, dyb1 = py1 - nx.y;
+                const float t0 = __saturatef(fmaf(dya0, c.w, dxa0 * c.z));
+                const float t1 = __saturatef(fmaf(dya1, c.w, dxa1 * c.z));
+                const float qx0 = fmaf(-t0, e.x, dxa0), qy0 = fmaf(-t0, e.y, dya0);
+                const float qx1 = fmaf(-t1, e.x, dxa1), qy1 = fmaf(-t1, e.y, dya1);
+                m0 = fminf(m0, fmaf(qy0, qy0, qx0 * qx0));
+                m1 = fminf(m1, fmaf(qy1, qy1, qx1 * qx1));
+                const float g0 = fmaf(dya0, e.z, -dxa0), g1 = fmaf(dya1, e.z, -dxa1);
+                const float X0 = dya0 * dyb0, X1 = dya1 * dyb1;
+                s0 ^= __float_as_uint(X0) & ~__float_as_uint(g0);
+                s1 ^= __float_as_uint(X1) & ~__float_as_uint(g1);
+                dxa0 = dxb0; dya0 = dyb0; dxa1 = dxb1; dya1 = dyb1;
+                c = nx;
+            }
+            k0 = __uint_as_float(__float_as_uint(m0) | (s0 & 0x80000000u));
+            k1 = __uint_as_float(__float_as_uint(m1) | (s1 & 0x80000000u));
+        } else {
+            float n0 = finf(), n1 = finf();
+            for (int j = 0; j < n; ++j) {
+                const float4 q = C[j];
+                const float ax0 = fabsf(px0 - q.x) - q.z, ay0 = fabsf(py0 - q.y) - q.w;
+                const float ax1 = fabsf(px1 - q.x) - q.z, ay1 = fabsf(py1 - q.y) - q.w;
+                const float ux0 = ax0 + fabsf(ax0), uy0 = ay0 + fabsf(ay0);
+                const float ux1 = ax1 + fabsf(ax1), uy1 = ay1 + fabsf(ay1);
+                n0 = fminf(n0, fmaf(uy0, uy0, ux0 * ux0));
+                n1 = fminf(n1, fmaf(uy1, uy1, ux1 * ux1));
+            }
+            float i0 = finf(), i1 = finf();
+            if (__any_sync(__activemask(), n0 == 0.f || n1 == 0.f)) {
+                for (int j = 0; j < n; ++j) {
+                    const float4 q = C[j];
+                    i0 = fminf(i0, fmaxf(fabsf(px0 - q.x) - q.z, fabsf(py0 - q.y) - q.w));
+                    i1 = fminf(i1, fmaxf(fabsf(px1 - q.x) - q.z, fabsf(py1 - q.y) - q.w));
+                }
+            }
+            k0 = rect_key(n0, i0);
+            k1 = rect_key(n1, i1);
+        }
+    }
+    __device__ __forceinline__ float dist(float key) const {
+        if (kind == EXACT_FP_POLYGON) {
+            const unsigned b = __float_as_uint(key);
+            return __uint_as_float(__float_as_uint(sqrtf(__uint_as_float(b & 0x7fffffffu))) | (b & 0x80000000u));
+        }
+        return rect_key_to_dist(key);
+    }
+};
+
+// ---------------------------------------------------------------- sample phase
+// Per-step minimum of the body-frame key over n staged points for the T
+// poses in shared memory.  Work items (step h, chunk of 32 * pairs_per_lane
+// point pairs) are dealt to the block's warps round-robin; each item ends
+// in one warp shuffle-min and one shared-memory atomicMin on the
+// order-preserving key of step h.  A ragged last pair repeats its first
+// point.  Masked points were staged as NaN, which every evaluator turns into
+// a +inf key (NaN terms are dropped by min, and the canonical NaN has a
+// clear sign bit, so it never toggles the crossing parity).
+template <class EV>
+__device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose, int T,
+                                               unsigned *keyh, int pairs_per_lane) {
+    const int npairs = (n + 1) >> 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int span = 32 * pairs_per_lane;
+    const int nchunk = npairs > 0 ? (npairs + span - 1) / span : 0;
+    const int items = T * nchunk;
+    for (int it = warp; it < items; it += nwarps) {
+        const int h = it / nchunk, c = it - h * nchunk;
+        const float4 q = pose[h];
+        float best = finf();
+        const int jend = min(npairs, (c + 1) * span);
+        for (int j = c * span + lane; j < jend; j += 32) {
+            const float2 o0 = pts[2 * j];
+            const float2 o1 = pts[min(2 * j + 1, n - 1)];
+            float px0, py0, px1, py1;
+            body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
+            body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
+            float k0, k1;
+            ev.eval2(px0, py0, px1, py1, k0, k1);
+            best = fmin3(best, k0, k1);
+        }
+        best = warp_min_f(best);
+        if (lane == 0) atomicMin(keyh + h, f2ord(best));
+    }
+}
+
+// Copy points [base, base + n) into shared memory, masked ones as NaN.
+// Eight loads per thread are in flight before the first store.
+__device__ __forceinline__ void stage_points(float2 *dst, const float2 *__restrict__ pts,
+                                             const uint8_t *__restrict__ mask, int base, int n, int t0, int nt) {
+    const float qnan = __int_as_float(0x7fffffff);
+    for (int i0 = t0; i0 < n; i0 += 8 * nt) {
+        float2 p[8];
+        bool ok[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k * nt;
+            p[k] = i < n ? __ldg(pts + base + i) : make_float2(0.f, 0.f);
+            ok[k] = i < n && (!mask || __ldg(mask + base + i));
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k * nt;
+            if (i < n) dst[i] = ok[k] ? p[k] : make_float2(qnan, qnan);
+        }
+    }
+}
+
+// phi_obs (Sec. IV-E) in double: its terms are large (w_coll scale) and are
+// summed over the horizon.
+__device__ __forceinline__ double phi_obs_d(const MppiP &P, float d) {
+    const double gap = fmax((double)P.d_safe - (double)d, 0.0);
+    return (d < 0.f ? (double)P.w_coll : 0.0) + (double)P.w_rep * gap * gap;
+}
+
+struct SampleSmem {
+    float4 pose[EXACT_MAX_HORIZON];
+    float stage[EXACT_MAX_HORIZON];
+    unsigned key[EXACT_MAX_HORIZON];
+    float term;
+};
+
+// One sample r of a scene.  s_pts holds min(N, kStage) points; when
+// `staged` is true the first chunk is already there (same scene as the
+// block's previous sample) and is not reloaded.  Ends with a __syncthreads.
+template <class EV>
+__device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, int r, SampleSmem &sm,
+                                            float2 *s_pts, bool staged, int pairs_per_lane) {
+    const MppiP &P = V.P;
+    const int T = P.T, nu = P.nu, N = V.N;
+    for (int h = threadIdx.x; h < T; h += blockDim.x) sm.key[h] = f2ord(finf());
+    const int n0 = min(N, kStage);
+    if (threadIdx.x < 32) {
+        const float *U = V.U;
+        const float *eps = V.noise + (size_t)r * T * nu;
+        LaneRollout R;
+        warp_rollout(P, V.state[0], V.state[1], V.state[2],
+                     [&](int h, int j) { return clamp_u(P, j, U[h * nu + j] + eps[h * nu + j]); }, R);
+        const int lane = threadIdx.x;
+#pragma unroll
+        for (int e = 0; e < kMaxPerLane; ++e) {
+            const int h = lane * R.per + e;
+            if (e < R.per && h < T) {
+                float sn, cs;
+                sincosf(R.th[e], &sn, &cs);
+                sm.pose[h] = make_float4(R.x[e], R.y[e], cs, sn);
+                const float u2 = fmaf(R.u[e][0], R.u[e][0], fmaf(R.u[e][1], R.u[e][1], R.u[e][2] * R.u[e][2]));
+                sm.stage[h] = fmaf(P.w_goal, guidance_dist(R.x[e], R.y[e], V.wp, V.W), P.w_ctrl * u2);
+            }
+        }
+        if (lane == 0) sm.term = P.w_term * guidance_dist(R.qTx, R.qTy, V.wp, V.W);
+    } else if (!staged) {
+        stage_points(s_pts, V.pts, V.mask, 0, n0, threadIdx.x - 32, blockDim.x - 32);
+    }
+    __syncthreads();
+    steps_min_keys(ev, s_pts, n0, sm.pose, T, sm.key, pairs_per_lane);
+    for (int base = kStage; base < N; base += kStage) {   // clouds larger than the stage
+        const int n = min(kStage, N - base);
+        __syncthreads();
+        stage_points(s_pts, V.pts, V.mask, base, n, threadIdx.x, blockDim.x);
+        __syncthreads();
+        steps_min_keys(ev, s_pts, n, sm.pose, T, sm.key, pairs_per_lane);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double acc = 0.0;
+        bool unsafe = false;
+        for (int h = threadIdx.x; h < T; h += 32) {
+            const float key = ord2f(sm.key[h]);
+            const float d = key == finf() ? finf() : ev.dist(key);
+            if (V.dmin) V.dmin[(size_t)r * T + h] = d;
+            acc += (double)sm.stage[h] + phi_obs_d(P, d);
+            unsafe |= d < P.d_safe;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const bool chi = __any_sync(0xffffffffu, unsafe);
+        if (threadIdx.x == 0) {
+            // J~ = J + w_inf I(chi) in double (Sec. IV-E); beta = min J~ is
+            // gathered with one 64-bit atomic per sample into the scene's
+            // header (complemented key; 0 = empty)
+            const double jt = acc + (double)sm.term + (chi ? (double)P.w_inf : 0.0);
+            V.Jt[r] = jt;
+            atomicMax(&V.hdr->beta_enc, ~d2ord(jt));
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- update phase
+struct UpdateSmem {
+    float tile[kUpdTile];
+    float w[256];
+    float f[kUpdBlock / 32];
+    float U[EXACT_MAX_HORIZON * 3];
+    float Z;
+    bool last;
+};
+
+// Chunk b of a scene's samples (blockDim == kUpdBlock): it stages its noise
+// rows (contiguous, coalesced, eight loads in flight per thread), forms
+// w_r = exp(-(J~_r - beta)/lambda) and sum_r w_r eps'_r, sum_r w_r into its
+// partial slot.  The scene's last chunk (atomic ticket) adds the partials,
+// writes the normalised weights, the costs and U_upd, and rolls the updated
+// nominal out for validation.
+__device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSmem &sm) {
+    const MppiP &P = V.P;
+    const int K = P.K, T = P.T, nu = P.nu, TN = T * nu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = b * V.upd_chunk, r1 = min(K, r0 + V.upd_chunk), nr = r1 - r0;
+    const float *U = V.U;
+    const double beta = ord2d(~V.hdr->beta_enc);
+
+    const float *src = V.noise + (size_t)r0 * TN;
+    const int n = nr * TN;
+    for (int i0 = tid; i0 < n; i0 += 8 * kUpdBlock) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k * kUpdBlock;
+            v[k] = i < n ? __ldg(src + i) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k * kUpdBlock;
+            if (i < n) {
+                const int e = i % TN;
+                sm.tile[i] = P.clamp ? clamp_u(P, e % nu, U[e] + v[k]) - U[e] : v[k];
+            }
+        }
+    }
+    float z = 0.f;
+    for (int i = tid; i < nr; i += kUpdBlock) {
+        const float w = expf(-(float)(V.Jt[r0 + i] - beta) / P.lambda);
+        sm.w[i] = w;
+        V.wt[r0 + i] = w;
+        z += w;
+    }
+    z = warp_sum_f(z);
+    if (lane == 0) sm.f[warp] = z;
+    __syncthreads();
+    float *part = V.part + (size_t)b * (TN + 1);
+    for (int e = tid; e < TN; e += kUpdBlock) {
+        float a0 = 0.f, a1 = 0.f;
+        int i = 0;
+        for (; i + 1 < nr; i += 2) {
+            a0 = fmaf(sm.w[i], sm.tile[i * TN + e], a0);
+            a1 = fmaf(sm.w[i + 1], sm.tile[(i + 1) * TN + e], a1);
+        }
+        if (i < nr) a0 = fmaf(sm.w[i], sm.tile[i * TN + e], a0);
+        part[e] = a0 + a1;
+    }
+    if (tid == 0) {
+        float zb = 0.f;
+        for (int w = 0; w < kUpdBlock / 32; ++w) zb += sm.f[w];
+        part[TN] = zb;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sm.last = atomicAdd(&V.hdr->ticket[0], 1u) == (unsigned)V.upd_blocks - 1;
+    __syncthreads();
+    if (!sm.last) return;
+    __threadfence();
+
+    const int G = V.upd_blocks;
+    if (warp == 0) {
+        float zz = 0.f;
+        for (int q = lane; q < G; q += 32) zz += __ldcg(V.part + (size_t)q * (TN + 1) + TN);
+        zz = warp_sum_f(zz);
+        if (lane == 0) sm.Z = zz;
+    }
+    __syncthreads();
+    const float invZ = 1.f / sm.Z;
+    for (int e = tid; e < TN; e += kUpdBlock) {
+        float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+        int q = 0;
+        for (; q + 3 < G; q += 4) {
+            t0 += __ldcg(V.part + (size_t)q * (TN + 1) + e);
+            t1 += __ldcg(V.part + (size_t)(q + 1) * (TN + 1) + e);
+            t2 += __ldcg(V.part + (size_t)(q + 2) * (TN + 1) + e);
+            t3 += __ldcg(V.part + (size_t)(q + 3) * (TN + 1) + e);
+        }
+        for (; q < G; ++q) t0 += __ldcg(V.part + (size_t)q * (TN + 1) + e);
+        const float v = U[e] + ((t0 + t1) + (t2 + t3)) * invZ;
+        sm.U[e] = v;
+        V.Uupd[e] = v;
+        if (V.U_upd_out) V.U_upd_out[e] = v;
+    }
+    if (V.weights || V.costs) {
+        for (int r = tid; r < K; r += kUpdBlock) {
+            if (V.weights) V.weights[r] = __ldcg(V.wt + r) * invZ;
+            if (V.costs) V.costs[r] = (float)V.Jt[r];
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        LaneRollout R;
+        warp_rollout(P, V.state[0], V.state[1], V.state[2], [&](int h, int j) { return clamp_u(P, j, sm.U[h * nu + j]); },
+                     R);
+#pragma unroll
+        for (int q = 0; q < kMaxPerLane; ++q) {
+            const int h = lane * R.per + q;
+            if (q < R.per && h < T) {
+                float sn, cs;
+                sincosf(R.th[q], &sn, &cs);
+                V.nom[h] = make_float4(R.x[q], R.y[q], cs, sn);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- validation
+struct ValidateSmem {
+    float mn[32];
+    bool last;
+};
+
+// Step h, point chunk c of the updated nominal.  The scene's last block
+// (atomic ticket) writes u*, the shifted (last entry repeated) or reset U,
+// the valid flag, and empties beta for the next cycle.
+template <class EV>
+__device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, int h, int c, ValidateSmem &sm) {
+    const MppiP &P = V.P;
+    const float4 q = V.nom[h];
+    const int N = V.N;
+    const int npairs = (N + 1) >> 1;
+    const int pend = min(npairs, (c + 1) * kValChunkPairs);
+    float best = finf();
+    for (int j = c * kValChunkPairs + threadIdx.x; j < pend; j += blockDim.x) {
+        const int i0 = 2 * j, i1 = min(2 * j + 1, N - 1);
+        const float2 o0 = __ldg(V.pts + i0);
+        const float2 o1 = __ldg(V.pts + i1);
+        float px0, py0, px1, py1;
+        body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
+        body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
+        float k0, k1;
+        ev.eval2(px0, py0, px1, py1, k0, k1);
+        if (V.mask) {
+            k0 = __ldg(V.mask + i0) ? k0 : finf();
+            k1 = __ldg(V.mask + i1) ? k1 : finf();
+        }
+        best = fmin3(best, k0, k1);
+    }
+    best = warp_min_f(best);
+    if ((threadIdx.x & 31) == 0) sm.mn[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = sm.mn[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fminf(b, sm.mn[w]);
+        const float d = b == finf() ? finf() : ev.dist(b);
+        if (!(d >= P.d_safe)) atomicExch(&V.hdr->bad, 1);
+        __threadfence();
+        sm.last = atomicAdd(&V.hdr->ticket[1], 1u) == (unsigned)(P.T * V.val_chunks) - 1;
+    }
+    __syncthreads();
+    if (!sm.last) return;
+    __threadfence();
+    const int ok = atomicAdd(&V.hdr->bad, 0) == 0;
+    const int T = P.T, nu = P.nu, TN = T * nu;
+    for (int e = threadIdx.x; e < TN; e += blockDim.x) {
+        const float v = __ldcg(V.Uupd + e);
+        if (e < nu && V.u_star) V.u_star[e] = ok ? v : 0.f;
+        V.U[e] = ok ? (e + nu < TN ? __ldcg(V.Uupd + e + nu) : v) : 0.f;
+    }
+    if (threadIdx.x == 0) {
+        if (V.valid) *V.valid = ok;
+        V.hdr->beta_enc = 0ull;
+    }
+}
+
+}  // namespace exact

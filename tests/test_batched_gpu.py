@@ -1,0 +1,127 @@
+"""Parity of mppi_step_batched (one persistent launch over many scenes) with
+the single-scene mppi_step path (bit for bit: same device bodies, same
+operation order) and with the FP64 oracle (the tolerances of
+test_mppi_gpu.py), on heterogeneous seeded scenes."""
+import numpy as np
+import pytest
+
+import synth
+from test_mppi_gpu import _t, compare, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ex():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_29663_gb300 import build
+    build.build()
+    import paper_2605_29663_gb300 as ex
+    return ex
+
+
+def _scene_set(seed, n, scale):
+    scenes = synth.batched(seed, n_scenes=n, scale=scale)
+    # a rectangle-cover forklift and a spin-in-place scene widen the mix
+    scenes.append(synth.forklift(seed, K=64, T=12, N=300))
+    s = synth.plain_step(seed + 1, K=40, T=9, N=77)
+    s["params"] = synth.mppi_params(40, 9, synth.SPIN)
+    s["U"] = np.zeros((9, 1), np.float32)
+    s["eps"] = synth.noise(synth.rng(seed + 2), 40, 9, (0.5,))
+    scenes.append(s)
+    return scenes
+
+
+def _dev_scene(ex, s):
+    return dict(state=_t(s["q0"]), cloud=_t(s["cloud"]), waypoints=_t(s["waypoints"]), U=_t(s["U"]),
+                noise=_t(s["eps"]), mask=None if s["mask"] is None else _t(s["mask"]),
+                fp=ex.Footprint(s["kind"], s["fp"]), params=s["params"])
+
+
+def _run_batched(ex, scenes, tiles=None):
+    import torch
+    dev = [_dev_scene(ex, s) for s in scenes]
+    b = ex.Batch(dev, dmin=True)
+    if tiles:
+        b.set_tiles(*tiles)
+    b.step()
+    torch.cuda.synchronize()
+    res = []
+    for d, o in zip(dev, b.outputs):
+        r = {k: v.cpu().numpy() for k, v in o.items()}
+        r["U"] = d["U"].cpu().numpy()
+        r["valid"] = bool(r["valid"][0])
+        res.append(r)
+    return res
+
+
+def _run_single(ex, ctx, s):
+    import torch
+    d = _dev_scene(ex, s)
+    out = ex.mppi_step(ctx, d["state"], d["cloud"], d["waypoints"], d["U"], d["noise"], d["fp"], s["params"],
+                       mask=d["mask"], dmin=True)
+    torch.cuda.synchronize()
+    r = {k: v.cpu().numpy() for k, v in out.items()}
+    r["U"] = d["U"].cpu().numpy()
+    r["valid"] = bool(r["valid"][0])
+    return r
+
+
+@pytest.mark.parametrize("tiles", [None, (128, 1), (512, 8)])
+def test_batched_equals_single_scene_bitwise(ex, tiles):
+    scenes = _scene_set(3, 10, 0.05)
+    got = _run_batched(ex, scenes, tiles)
+    ctx = ex.Context()
+    for i, s in enumerate(scenes):
+        ref = _run_single(ex, ctx, s)
+        for key in ("dmin", "costs", "weights", "U_upd", "U", "u_star"):
+            np.testing.assert_array_equal(got[i][key], ref[key], err_msg=f"scene {i} {key}")
+        assert got[i]["valid"] == ref["valid"]
+
+
+def test_batched_matches_oracle(ex):
+    scenes = [s for s in _scene_set(5, 8, 0.03)]
+    got = _run_batched(ex, scenes)
+    checked = 0
+    for s, g in zip(scenes, got):
+        o = run_oracle(s)
+        if o["n_near"]:
+            continue
+        compare(s, g, o)
+        checked += 1
+    assert checked >= len(scenes) - 3
+
+
+def test_batched_two_steps_and_autotune(ex):
+    """A second step on the same plan (state carried in U) still equals the
+    single-scene path; autotuning touches no scene output."""
+    import torch
+    scenes = _scene_set(7, 6, 0.04)
+    dev = [_dev_scene(ex, s) for s in scenes]
+    b = ex.Batch(dev, dmin=False)
+    U0 = [d["U"].clone() for d in dev]
+    report = b.autotune(iters=1)
+    assert report["best"]["threads"] in (128, 256, 512) and len(report["candidates"]) >= 6
+    for d, u in zip(dev, U0):
+        assert torch.equal(d["U"], u)
+    b.step()
+    b.step()
+    torch.cuda.synchronize()
+    ctx = ex.Context()
+    for i, s in enumerate(scenes):
+        d = _dev_scene(ex, s)
+        for _ in range(2):
+            ex.mppi_step(ctx, d["state"], d["cloud"], d["waypoints"], d["U"], d["noise"], d["fp"], s["params"],
+                         mask=d["mask"])
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(dev[i]["U"].cpu().numpy(), d["U"].cpu().numpy(), err_msg=f"scene {i}")
+
+
+def test_batch_rejects_bad_scene(ex):
+    s = synth.plain_step(0, K=8, T=4, N=16)
+    d = _dev_scene(ex, s)
+    d["params"] = dict(s["params"], nu=3)        # wrong control dimension for diff-drive
+    with pytest.raises(ex.ExactError):
+        ex.Batch([d])
