@@ -67,7 +67,7 @@ batched_sample_kernel(const SceneDev *__restrict__ scenes, const int2 *__restric
             fp_scene = it.x;
         }
         const SmemEval ev{s_fp, D.kind, D.nfp};
-        sample_body(D.V, ev, it.y, sm, s_pts, it.x == pts_scene, pairs_per_lane);
+        sample_body(D.V, ev, it.y, 0, sm, s_pts, it.x == pts_scene, pairs_per_lane);
         pts_scene = D.V.N <= kStage ? it.x : -1;
     }
 }
@@ -138,7 +138,7 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
             return EXACT_EINVAL;
         if (S.n_points > 0 && (!S.cloud || ((uintptr_t)S.cloud & 7u) != 0)) return EXACT_EINVAL;
         scratch_off[s] = scratch_total;
-        scratch_total += align_up(scene_scratch_bytes(S.params.K, S.params.T), 256);
+        scratch_total += align_up(scene_scratch_bytes(S.params.K, S.params.T, 1), 256);
         max_stage = std::max(max_stage, std::min(S.n_points, kStage));
     }
     const size_t table_bytes = align_up(sizeof(SceneDev) * n_scenes, 256);
@@ -201,7 +201,7 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         V.u_star = S.u_star; V.costs = S.costs; V.weights = S.weights; V.U_upd_out = S.U_upd;
         V.dmin = S.dmin; V.valid = S.valid;
         V.hdr = reinterpret_cast<ArenaHeader *>(b->d_ctrl + kHdrStride * s);
-        carve_scene(V, scratch + scratch_off[s], S.params.K, S.params.T);
+        carve_scene(V, scratch + scratch_off[s], S.params.K, S.params.T, 1);
         V.upd_chunk = upd_chunk_for(S.params.T, S.params.n_u);
         V.upd_blocks = upd_blocks_for(S.params.K, S.params.T, S.params.n_u);
         V.val_chunks = val_chunks_for(S.n_points);

@@ -134,54 +134,38 @@ __device__ __forceinline__ void poly_eval2(const PolyC<E> &P, float px0, float p
 // so the evaluator tracks 4 |max(a,0)|^2 and halves the root at the end:
 // both scalings by powers of two are exact.
 template <int R, int J>
-__device__ __forceinline__ float rect_n4(const RectC<R> &Q, float px, float py) {
+__device__ __forceinline__ void rect_box(const RectC<R> &Q, float px, float py, float &n4, float &mx2) {
     const float ax = fabsf(px - Q.cx[J]) - Q.sx[J];
     const float ay = fabsf(py - Q.cy[J]) - Q.sy[J];
     const float ux = ax + fabsf(ax), uy = ay + fabsf(ay);
-    return fmaf(uy, uy, ux * ux);
-}
-template <int R, int J>
-__device__ __forceinline__ float rect_depth(const RectC<R> &Q, float px, float py) {
-    return fmaxf(fabsf(px - Q.cx[J]) - Q.sx[J], fabsf(py - Q.cy[J]) - Q.sy[J]);
+    n4 = fmaf(uy, uy, ux * ux);
+    mx2 = fmaxf(ax, ay);
 }
 
 template <int R, int J>
-__device__ __forceinline__ void rect_outer(const RectC<R> &Q, float px, float py, float &nn) {
+__device__ __forceinline__ void rect_boxes(const RectC<R> &Q, float px, float py, float &nn, float &in) {
     if constexpr (J + 1 < R) {
-        nn = fmin3(nn, rect_n4<R, J>(Q, px, py), rect_n4<R, J + 1>(Q, px, py));
-        rect_outer<R, J + 2>(Q, px, py, nn);
+        float na, ia, nb, ib;
+        rect_box<R, J>(Q, px, py, na, ia);
+        rect_box<R, J + 1>(Q, px, py, nb, ib);
+        nn = fmin3(nn, na, nb);
+        in = fmin3(in, ia, ib);
+        rect_boxes<R, J + 2>(Q, px, py, nn, in);
     } else if constexpr (J < R) {
-        nn = fminf(nn, rect_n4<R, J>(Q, px, py));
-    }
-}
-template <int R, int J>
-__device__ __forceinline__ void rect_inner(const RectC<R> &Q, float px, float py, float &in) {
-    if constexpr (J + 1 < R) {
-        in = fmin3(in, rect_depth<R, J>(Q, px, py), rect_depth<R, J + 1>(Q, px, py));
-        rect_inner<R, J + 2>(Q, px, py, in);
-    } else if constexpr (J < R) {
-        in = fminf(in, rect_depth<R, J>(Q, px, py));
+        float na, ia;
+        rect_box<R, J>(Q, px, py, na, ia);
+        nn = fminf(nn, na);
+        in = fminf(in, ia);
     }
 }
 
-// n4 = min_j 4 |max(a_j, 0)|^2 and inner = min_j max(a_jx, a_jy) of two
-// points.  inner matters only where n4 == 0 (the point lies in or on some
-// box); its pass runs when any lane of the warp has such a point, so warps
-// whose points are all outside skip it (the values are identical either way).
+// n4 = min_j 4 |max(a_j, 0)|^2, inner = min_j max(a_jx, a_jy).
 template <int R>
-__device__ __forceinline__ void rect_eval2(const RectC<R> &Q, float px0, float py0, float px1, float py1,
-                                           float &n0, float &i0, float &n1, float &i1) {
-    float a = finf(), b = finf();
-    rect_outer<R, 0>(Q, px0, py0, a);
-    rect_outer<R, 0>(Q, px1, py1, b);
-    n0 = a;
-    n1 = b;
-    i0 = finf();
-    i1 = finf();
-    if (__any_sync(__activemask(), a == 0.f || b == 0.f)) {
-        rect_inner<R, 0>(Q, px0, py0, i0);
-        rect_inner<R, 0>(Q, px1, py1, i1);
-    }
+__device__ __forceinline__ void rect_eval(const RectC<R> &Q, float px, float py, float &n4, float &inner) {
+    float nn = finf(), in = finf();
+    rect_boxes<R, 0>(Q, px, py, nn, in);
+    n4 = nn;
+    inner = in;
 }
 // Mixed key: the (negative) depth inside, 4 x the squared distance outside.
 __device__ __forceinline__ float rect_key(float n4, float inner) { return inner < 0.f ? inner : n4; }
@@ -241,7 +225,8 @@ template <int R>
 __device__ __forceinline__ void eval2(const RectC<R> &Q, float px0, float py0, float px1, float py1,
                                       float &k0, float &k1) {
     float n0, i0, n1, i1;
-    rect_eval2(Q, px0, py0, px1, py1, n0, i0, n1, i1);
+    rect_eval(Q, px0, py0, n0, i0);
+    rect_eval(Q, px1, py1, n1, i1);
     k0 = rect_key(n0, i0);
     k1 = rect_key(n1, i1);
 }

@@ -27,6 +27,7 @@ struct exact_ctx {
     void *scratch = nullptr;     // growable device arena
     size_t scratch_bytes = 0;
     int *d_err = nullptr;        // device error word (exact_status)
+    long long mppi_layout = -1;  // (K, T, parts) of the last mppi_step; -1 = arena reused otherwise
 };
 
 namespace exact {
@@ -36,7 +37,6 @@ int ensure_scratch(exact_ctx *ctx, size_t bytes);
 int current_sm_count();
 // Arena bytes needed by exact_sdf_batch (n_poses) and mppi_step (K, T).
 size_t sdf_scratch_bytes(int n_poses);
-size_t mppi_scratch_bytes(int K, int T);
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 

@@ -1,9 +1,11 @@
 // mppi.cu -- mppi_step: one EXACT-MPPI control cycle (Algorithm 1) for one
 // robot, as three stream-ordered kernels (capturable in one CUDA graph):
-//   mppi_sample_kernel    K blocks, one per sample (sample_body): warp 0 rolls
+//   mppi_sample_kernel    K x parts blocks (sample_body): warp 0 rolls
 //                         the sample out while the other warps stage the
 //                         obstacle points in shared memory, then every
-//                         (step, point) signed distance, then J~.
+//                         (step, point) signed distance, then J~; when K
+//                         is small each sample's horizon is split over
+//                         several blocks (parts) to fill the GPU.
 //   mppi_update_kernel    ceil(K / chunk) blocks (update_body): weights and
 //                         weighted clipped noise; the last block sums them,
 //                         writes U_upd and rolls the updated nominal out.
@@ -29,7 +31,7 @@ mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev) {
         V.hdr->ticket[1] = 0u;
         V.hdr->bad = 0;
     }
-    sample_body(V, ev, blockIdx.x, sm, s_pts, false, 4);
+    sample_body(V, ev, blockIdx.x / V.parts, blockIdx.x % V.parts, sm, s_pts, false, 4);
 }
 
 __global__ void __launch_bounds__(kUpdBlock) mppi_update_kernel(const SceneView V) {
@@ -43,7 +45,9 @@ __global__ void __launch_bounds__(kBlock) mppi_validate_kernel(const SceneView V
     validate_body(V, ev, blockIdx.x / V.val_chunks, blockIdx.x % V.val_chunks, sm);
 }
 
-size_t mppi_scratch_bytes(int K, int T) { return kArenaHeader + scene_scratch_bytes(K, T); }
+static int parts_of(const exact_ctx *ctx, int K, int T) {
+    return parts_for(K, T, 8 * (ctx->sm_count > 0 ? ctx->sm_count : 148));
+}
 
 int check_params(const exact_mppi_params *p) {
     if (!p) return EXACT_EINVAL;
@@ -76,7 +80,7 @@ using namespace exact;
 extern "C" int exact_ctx_reserve(exact_ctx *ctx, int max_poses, int max_K, int max_T) {
     if (!ctx || max_poses < 0 || max_K < 0 || max_T < 0) return EXACT_EINVAL;
     size_t need = sdf_scratch_bytes(max_poses);
-    const size_t m = mppi_scratch_bytes(max_K, max_T);
+    const size_t m = kArenaHeader + scene_scratch_bytes(max_K, max_T, parts_of(ctx, max_K, max_T));
     if (m > need) need = m;
     return ensure_scratch(ctx, need);
 }
@@ -91,7 +95,8 @@ extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud,
     int rc = check_params(params);
     if (rc != EXACT_OK) return rc;
     const MppiP P = to_device_params(params);
-    rc = ensure_scratch(ctx, mppi_scratch_bytes(P.K, P.T));
+    const int parts = parts_of(ctx, P.K, P.T);
+    rc = ensure_scratch(ctx, kArenaHeader + scene_scratch_bytes(P.K, P.T, parts));
     if (rc != EXACT_OK) return rc;
     SceneView V;
     V.P = P;
@@ -105,16 +110,23 @@ extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud,
     V.noise = noise;
     V.u_star = u_star; V.costs = costs; V.weights = weights; V.U_upd_out = U_upd; V.dmin = dmin; V.valid = valid;
     V.hdr = reinterpret_cast<ArenaHeader *>(ctx->scratch);
-    carve_scene(V, static_cast<char *>(ctx->scratch) + kArenaHeader, P.K, P.T);
+    carve_scene(V, static_cast<char *>(ctx->scratch) + kArenaHeader, P.K, P.T, parts);
     V.upd_chunk = upd_chunk_for(P.T, P.nu);
     V.upd_blocks = upd_blocks_for(P.K, P.T, P.nu);
     V.val_chunks = val_chunks_for(n_points);
     cudaStream_t st = (cudaStream_t)stream;
+    // the per-sample part tickets rearm themselves after each cycle; zero
+    // them once whenever the arena layout changes
+    const long long layout = ((long long)P.K << 24) ^ ((long long)P.T << 8) ^ V.parts;
+    if (V.parts > 1 && ctx->mppi_layout != layout) {
+        if (cudaMemsetAsync(V.tk, 0, (size_t)P.K * sizeof(unsigned), st) != cudaSuccess) return EXACT_ECUDA;
+    }
+    ctx->mppi_layout = layout;
     const size_t smem = (size_t)min(n_points, kStage) * sizeof(float2);
     return with_footprint(fp, [&](auto fpc) -> int {
         using FPC = decltype(fpc);
         const ConstEval<FPC> ev{fpc};
-        mppi_sample_kernel<FPC><<<P.K, kBlock, smem, st>>>(V, ev);
+        mppi_sample_kernel<FPC><<<P.K * V.parts, kBlock, smem, st>>>(V, ev);
         mppi_update_kernel<<<V.upd_blocks, kUpdBlock, 0, st>>>(V);
         mppi_validate_kernel<FPC><<<P.T * V.val_chunks, kBlock, 0, st>>>(V, ev);
         return cuda_status(cudaGetLastError());

@@ -44,7 +44,10 @@ struct SceneView {
     float *part;        // G x (T*nu + 1) partial sums
     float *Uupd;        // T x nu
     float4 *nom;        // T   scored nominal states (x, y, cos, sin)
+    unsigned *dkey;     // K x T  per-step keys exchanged between horizon parts
+    unsigned *tk;       // K      finished horizon parts of each sample
     int upd_chunk, upd_blocks, val_chunks;
+    int parts;          // blocks per sample (horizon split); 1 = one block per sample
 };
 
 // samples per update block: the block's noise tile fits kUpdTile floats
@@ -61,22 +64,43 @@ inline int val_chunks_for(int N) {
     return np > kValChunkPairs ? (np + kValChunkPairs - 1) / kValChunkPairs : 1;
 }
 
+// Blocks per sample: split the horizon when there are too few samples to
+// fill the GPU (about `target` blocks), at most 8 parts and one step each.
+inline int parts_for(int K, int T, int target) {
+    if (K >= target) return 1;
+    int p = (target + K - 1) / K;
+    if (p > 8) p = 8;
+    if (p > T) p = T;
+    return p < 1 ? 1 : p;
+}
+
 // Per-scene arena bytes after the header (n_u = 3 bounds the update blocks).
-inline size_t scene_scratch_bytes(int K, int T) {
+inline size_t scene_scratch_bytes(int K, int T, int parts) {
     size_t b = 0;
     b += align_up((size_t)K * sizeof(double), 256);
     b += align_up((size_t)K * sizeof(float), 256);
     b += align_up((size_t)upd_blocks_for(K, T, 3) * (T * 3 + 1) * sizeof(float), 256);
     b += align_up((size_t)T * 3 * sizeof(float), 256);
     b += align_up((size_t)T * sizeof(float4), 256);
+    if (parts > 1) {
+        b += align_up((size_t)K * T * sizeof(unsigned), 256);
+        b += align_up((size_t)K * sizeof(unsigned), 256);
+    }
     return b;
 }
-inline void carve_scene(SceneView &V, char *p, int K, int T) {
+inline void carve_scene(SceneView &V, char *p, int K, int T, int parts) {
     V.Jt = reinterpret_cast<double *>(p); p += align_up((size_t)K * sizeof(double), 256);
     V.wt = reinterpret_cast<float *>(p); p += align_up((size_t)K * sizeof(float), 256);
     V.part = reinterpret_cast<float *>(p); p += align_up((size_t)upd_blocks_for(K, T, 3) * (T * 3 + 1) * sizeof(float), 256);
     V.Uupd = reinterpret_cast<float *>(p); p += align_up((size_t)T * 3 * sizeof(float), 256);
-    V.nom = reinterpret_cast<float4 *>(p);
+    V.nom = reinterpret_cast<float4 *>(p); p += align_up((size_t)T * sizeof(float4), 256);
+    V.parts = parts;
+    V.dkey = nullptr;
+    V.tk = nullptr;
+    if (parts > 1) {
+        V.dkey = reinterpret_cast<unsigned *>(p); p += align_up((size_t)K * T * sizeof(unsigned), 256);
+        V.tk = reinterpret_cast<unsigned *>(p);
+    }
 }
 
 // Order-preserving map of a double onto uint64 (total order).
@@ -134,7 +158,7 @@ struct SmemEval {
             k0 = __uint_as_float(__float_as_uint(m0) | (s0 & 0x80000000u));
             k1 = __uint_as_float(__float_as_uint(m1) | (s1 & 0x80000000u));
         } else {
-            float n0 = finf(), n1 = finf();
+            float n0 = finf(), n1 = finf(), i0 = finf(), i1 = finf();
             for (int j = 0; j < n; ++j) {
                 const float4 q = C[j];
                 const float ax0 = fabsf(px0 - q.x) - q.z, ay0 = fabsf(py0 - q.y) - q.w;
@@ -143,14 +167,8 @@ struct SmemEval {
                 const float ux1 = ax1 + fabsf(ax1), uy1 = ay1 + fabsf(ay1);
                 n0 = fminf(n0, fmaf(uy0, uy0, ux0 * ux0));
                 n1 = fminf(n1, fmaf(uy1, uy1, ux1 * ux1));
-            }
-            float i0 = finf(), i1 = finf();
-            if (__any_sync(__activemask(), n0 == 0.f || n1 == 0.f)) {
-                for (int j = 0; j < n; ++j) {
-                    const float4 q = C[j];
-                    i0 = fminf(i0, fmaxf(fabsf(px0 - q.x) - q.z, fabsf(py0 - q.y) - q.w));
-                    i1 = fminf(i1, fmaxf(fabsf(px1 - q.x) - q.z, fabsf(py1 - q.y) - q.w));
-                }
+                i0 = fminf(i0, fmaxf(ax0, ay0));
+                i1 = fminf(i1, fmaxf(ax1, ay1));
             }
             k0 = rect_key(n0, i0);
             k1 = rect_key(n1, i1);
@@ -175,15 +193,16 @@ struct SmemEval {
 // a +inf key (NaN terms are dropped by min, and the canonical NaN has a
 // clear sign bit, so it never toggles the crossing parity).
 template <class EV>
-__device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose, int T,
-                                               unsigned *keyh, int pairs_per_lane) {
+__device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose, int h0,
+                                               int nh, unsigned *keyh, int pairs_per_lane) {
     const int npairs = (n + 1) >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int span = 32 * pairs_per_lane;
     const int nchunk = npairs > 0 ? (npairs + span - 1) / span : 0;
-    const int items = T * nchunk;
+    const int items = nh * nchunk;
     for (int it = warp; it < items; it += nwarps) {
-        const int h = it / nchunk, c = it - h * nchunk;
+        const int hh = it / nchunk, c = it - hh * nchunk;
+        const int h = h0 + hh;
         const float4 q = pose[h];
         float best = finf();
         const int jend = min(npairs, (c + 1) * span);
@@ -236,17 +255,24 @@ struct SampleSmem {
     float stage[EXACT_MAX_HORIZON];
     unsigned key[EXACT_MAX_HORIZON];
     float term;
+    bool last;
 };
 
-// One sample r of a scene.  s_pts holds min(N, kStage) points; when
-// `staged` is true the first chunk is already there (same scene as the
-// block's previous sample) and is not reloaded.  Ends with a __syncthreads.
+// Horizon part p of sample r of a scene (steps [p T / parts, (p+1) T / parts)).
+// s_pts holds min(N, kStage) points; when `staged` is true the first chunk
+// is already there (same scene as the block's previous sample) and is not
+// reloaded.  With several parts, each publishes its per-step keys and the
+// last part of the sample (atomic ticket) gathers the others' and forms J~
+// exactly as a single block would (same per-step data, same summation
+// order), so the split never changes a bit of the result.  Ends with a
+// __syncthreads.
 template <class EV>
-__device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, int r, SampleSmem &sm,
+__device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, int r, int p, SampleSmem &sm,
                                             float2 *s_pts, bool staged, int pairs_per_lane) {
     const MppiP &P = V.P;
     const int T = P.T, nu = P.nu, N = V.N;
-    for (int h = threadIdx.x; h < T; h += blockDim.x) sm.key[h] = f2ord(finf());
+    const int h0 = (p * T) / V.parts, h1 = ((p + 1) * T) / V.parts;
+    for (int h = h0 + (int)threadIdx.x; h < h1; h += blockDim.x) sm.key[h] = f2ord(finf());
     const int n0 = min(N, kStage);
     if (threadIdx.x < 32) {
         const float *U = V.U;
@@ -271,15 +297,27 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
         stage_points(s_pts, V.pts, V.mask, 0, n0, threadIdx.x - 32, blockDim.x - 32);
     }
     __syncthreads();
-    steps_min_keys(ev, s_pts, n0, sm.pose, T, sm.key, pairs_per_lane);
+    steps_min_keys(ev, s_pts, n0, sm.pose, h0, h1 - h0, sm.key, pairs_per_lane);
     for (int base = kStage; base < N; base += kStage) {   // clouds larger than the stage
         const int n = min(kStage, N - base);
         __syncthreads();
         stage_points(s_pts, V.pts, V.mask, base, n, threadIdx.x, blockDim.x);
         __syncthreads();
-        steps_min_keys(ev, s_pts, n, sm.pose, T, sm.key, pairs_per_lane);
+        steps_min_keys(ev, s_pts, n, sm.pose, h0, h1 - h0, sm.key, pairs_per_lane);
     }
     __syncthreads();
+    if (V.parts > 1) {
+        for (int h = h0 + (int)threadIdx.x; h < h1; h += blockDim.x) V.dkey[(size_t)r * T + h] = sm.key[h];
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) sm.last = atomicAdd(V.tk + r, 1u) == (unsigned)V.parts - 1;
+        __syncthreads();
+        if (!sm.last) return;
+        __threadfence();
+        for (int h = threadIdx.x; h < T; h += blockDim.x)
+            if (h < h0 || h >= h1) sm.key[h] = __ldcg(V.dkey + (size_t)r * T + h);
+        __syncthreads();
+    }
     if (threadIdx.x < 32) {
         double acc = 0.0;
         bool unsafe = false;
@@ -347,6 +385,8 @@ __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSme
             }
         }
     }
+    if (V.parts > 1)   // the sample phase is over: rearm its per-sample part tickets
+        for (int i = tid; i < nr; i += kUpdBlock) V.tk[r0 + i] = 0u;
     float z = 0.f;
     for (int i = tid; i < nr; i += kUpdBlock) {
         const float w = expf(-(float)(V.Jt[r0 + i] - beta) / P.lambda);

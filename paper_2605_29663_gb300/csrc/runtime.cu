@@ -186,6 +186,7 @@ int ensure_scratch(exact_ctx *ctx, size_t bytes) {
     // counters and flags in the arena must start at zero
     if (cudaMemset(ctx->scratch, 0, bytes) != cudaSuccess) return EXACT_ECUDA;
     ctx->scratch_bytes = bytes;
+    ctx->mppi_layout = -1;
     return EXACT_OK;
 }
 

@@ -135,6 +135,7 @@ extern "C" int exact_sdf_batch(exact_ctx *ctx, const float *points, const uint8_
         const int rc = ensure_scratch(ctx, sdf_scratch_bytes(n_poses));
         if (rc != EXACT_OK) return rc;
         keys = reinterpret_cast<unsigned long long *>(static_cast<char *>(ctx->scratch) + kArenaHeader);
+        ctx->mppi_layout = -1;   // the keys overlay the MPPI per-sample counters
         sdf_keys_init<<<(n_poses + 255) / 256, 256, 0, st>>>(keys, n_poses);
     }
     const float2 *p2 = reinterpret_cast<const float2 *>(points);

@@ -122,6 +122,6 @@ def test_batched_two_steps_and_autotune(ex):
 def test_batch_rejects_bad_scene(ex):
     s = synth.plain_step(0, K=8, T=4, N=16)
     d = _dev_scene(ex, s)
-    d["params"] = dict(s["params"], nu=3)        # wrong control dimension for diff-drive
+    d["params"] = dict(s["params"], **{"lambda": 0.0})   # the temperature must be positive
     with pytest.raises(ex.ExactError):
         ex.Batch([d])
