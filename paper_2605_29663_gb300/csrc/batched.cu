@@ -202,7 +202,7 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         V.dmin = S.dmin; V.valid = S.valid;
         V.hdr = reinterpret_cast<ArenaHeader *>(b->d_ctrl + kHdrStride * s);
         carve_scene(V, scratch + scratch_off[s], S.params.K, S.params.T, 1);
-        V.upd_chunk = upd_chunk_for(S.params.T, S.params.n_u);
+        V.upd_chunk = upd_chunk_for(S.params.K, S.params.T, S.params.n_u);
         V.upd_blocks = upd_blocks_for(S.params.K, S.params.T, S.params.n_u);
         V.val_chunks = val_chunks_for(S.n_points);
         const exact_footprint *fp = S.fp;

@@ -46,7 +46,24 @@ __global__ void __launch_bounds__(kBlock) mppi_validate_kernel(const SceneView V
 }
 
 static int parts_of(const exact_ctx *ctx, int K, int T) {
-    return parts_for(K, T, 8 * (ctx->sm_count > 0 ? ctx->sm_count : 148));
+    return parts_for(K, T, ctx->sm_count > 0 ? ctx->sm_count : 148);
+}
+
+// Launch with the programmatic-serialization attribute (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                                    cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 int check_params(const exact_mppi_params *p) {
@@ -111,7 +128,7 @@ extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud,
     V.u_star = u_star; V.costs = costs; V.weights = weights; V.U_upd_out = U_upd; V.dmin = dmin; V.valid = valid;
     V.hdr = reinterpret_cast<ArenaHeader *>(ctx->scratch);
     carve_scene(V, static_cast<char *>(ctx->scratch) + kArenaHeader, P.K, P.T, parts);
-    V.upd_chunk = upd_chunk_for(P.T, P.nu);
+    V.upd_chunk = upd_chunk_for(P.K, P.T, P.nu);
     V.upd_blocks = upd_blocks_for(P.K, P.T, P.nu);
     V.val_chunks = val_chunks_for(n_points);
     cudaStream_t st = (cudaStream_t)stream;
@@ -127,8 +144,10 @@ extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud,
         using FPC = decltype(fpc);
         const ConstEval<FPC> ev{fpc};
         mppi_sample_kernel<FPC><<<P.K * V.parts, kBlock, smem, st>>>(V, ev);
-        mppi_update_kernel<<<V.upd_blocks, kUpdBlock, 0, st>>>(V);
-        mppi_validate_kernel<FPC><<<P.T * V.val_chunks, kBlock, 0, st>>>(V, ev);
-        return cuda_status(cudaGetLastError());
+        if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
+        if (launch_dependent(mppi_update_kernel, V.upd_blocks, kUpdBlock, 0, st, V) != cudaSuccess) return EXACT_ECUDA;
+        if (launch_dependent(mppi_validate_kernel<FPC>, P.T * V.val_chunks, kBlock, 0, st, V, ev) != cudaSuccess)
+            return EXACT_ECUDA;
+        return EXACT_OK;
     });
 }

@@ -50,15 +50,28 @@ struct SceneView {
     int parts;          // blocks per sample (horizon split); 1 = one block per sample
 };
 
-// samples per update block: the block's noise tile fits kUpdTile floats
-inline int upd_chunk_for(int T, int nu) {
-    const int c = kUpdTile / (T * nu);
-    return c < 1 ? 1 : (c > 256 ? 256 : c);
+// samples per update block: the block's noise tile fits kUpdTile floats,
+// and K is spread over about 64 blocks (at least 8 samples each) so that
+// the tiles load in parallel
+inline int upd_chunk_for(int K, int T, int nu) {
+    int c = kUpdTile / (T * nu);
+    if (c > 256) c = 256;
+    int spread = (K + 63) / 64;
+    if (spread < 8) spread = 8;
+    if (c > spread) c = spread;
+    return c < 1 ? 1 : c;
 }
 inline int upd_blocks_for(int K, int T, int nu) {
-    const int c = upd_chunk_for(T, nu);
+    const int c = upd_chunk_for(K, T, nu);
     return (K + c - 1) / c;
 }
+
+// Programmatic dependent launch (sm_90+): a kernel launched with the
+// programmatic-serialization attribute may start while its predecessor on
+// the stream drains; grid_dep_wait blocks until the predecessor has
+// completed and its writes are visible (a no-op without the attribute).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 inline int val_chunks_for(int N) {
     const int np = (N + 1) / 2;
     return np > kValChunkPairs ? (np + kValChunkPairs - 1) / kValChunkPairs : 1;
@@ -74,7 +87,7 @@ inline int parts_for(int K, int T, int target) {
     return p < 1 ? 1 : p;
 }
 
-// Per-scene arena bytes after the header (n_u = 3 bounds the update blocks).
+// Per-scene arena bytes after the header (n_u = 3 gives the most update blocks).
 inline size_t scene_scratch_bytes(int K, int T, int parts) {
     size_t b = 0;
     b += align_up((size_t)K * sizeof(double), 256);
@@ -305,6 +318,7 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
         __syncthreads();
         steps_min_keys(ev, s_pts, n, sm.pose, h0, h1 - h0, sm.key, pairs_per_lane);
     }
+    grid_dep_release();
     __syncthreads();
     if (V.parts > 1) {
         for (int h = h0 + (int)threadIdx.x; h < h1; h += blockDim.x) V.dkey[(size_t)r * T + h] = sm.key[h];
@@ -365,7 +379,6 @@ __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSme
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r0 = b * V.upd_chunk, r1 = min(K, r0 + V.upd_chunk), nr = r1 - r0;
     const float *U = V.U;
-    const double beta = ord2d(~V.hdr->beta_enc);
 
     const float *src = V.noise + (size_t)r0 * TN;
     const int n = nr * TN;
@@ -385,6 +398,8 @@ __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSme
             }
         }
     }
+    grid_dep_wait();   // J~ and beta come from the sample phase
+    const double beta = ord2d(~V.hdr->beta_enc);
     if (V.parts > 1)   // the sample phase is over: rearm its per-sample part tickets
         for (int i = tid; i < nr; i += kUpdBlock) V.tk[r0 + i] = 0u;
     float z = 0.f;
@@ -416,6 +431,7 @@ __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSme
     __threadfence();
     __syncthreads();
     if (tid == 0) sm.last = atomicAdd(&V.hdr->ticket[0], 1u) == (unsigned)V.upd_blocks - 1;
+    grid_dep_release();
     __syncthreads();
     if (!sm.last) return;
     __threadfence();
@@ -479,6 +495,7 @@ struct ValidateSmem {
 template <class EV>
 __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, int h, int c, ValidateSmem &sm) {
     const MppiP &P = V.P;
+    grid_dep_wait();   // the nominal comes from the update phase
     const float4 q = V.nom[h];
     const int N = V.N;
     const int npairs = (N + 1) >> 1;
