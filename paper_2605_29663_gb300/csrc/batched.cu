@@ -15,8 +15,11 @@
 //                           in shared memory (reloaded only when the scene
 //                           changes; so are the staged points when the cloud
 //                           fits the stage);
-//   batched_update_kernel   one block per (scene, sample chunk);
-//   batched_validate_kernel one block per (scene, step, point chunk).
+//   batched_update_kernel   one block per (scene, sample chunk): weights and
+//                           weighted noise into the scene's partial slots;
+//   batched_validate_kernel one block per (scene, step, point chunk): U_upd
+//                           from the partial slots, the nominal rollout, the
+//                           clearance check and the scene's shift / reset.
 // The per-scene arithmetic is that of mppi_step (same device bodies, same
 // operation order), so a scene of a batch gives the same bits as mppi_step.
 #include <stdio.h>

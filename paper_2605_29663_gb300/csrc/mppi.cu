@@ -7,11 +7,15 @@
 //                         is small each sample's horizon is split over
 //                         several blocks (parts) to fill the GPU.
 //   mppi_update_kernel    ceil(K / chunk) blocks (update_body): weights and
-//                         weighted clipped noise; the last block sums them,
-//                         writes U_upd and rolls the updated nominal out.
-//   mppi_validate_kernel  T x ceil(N / 2048) blocks (validate_body): the
-//                         nominal's clearance; the last block writes u*, the
-//                         shifted or reset U and the valid flag.
+//                         weighted clipped noise into per-block partial slots.
+//   mppi_validate_kernel  T x ceil(N / 2048) blocks (validate_body): each adds
+//                         the partial slots (U_upd), rolls the updated nominal
+//                         out to its step and checks its clearance; the last
+//                         block writes u*, the shifted or reset U and the
+//                         valid flag.
+// The update and validation kernels use programmatic dependent launch: each
+// starts while its predecessor drains and waits (griddepcontrol) only where
+// it reads the predecessor's results.
 // The footprint constants are kernel parameters (compile-time edge count).
 // No K x T x N intermediate exists; scratch is per-sample J~ / weights,
 // per-block partial sums and per-step nominal data in the context arena.
@@ -25,9 +29,8 @@ mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev) {
     extern __shared__ float2 s_pts[];   // min(N, kStage) staged points
     __shared__ SampleSmem sm;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        // the update and validation kernels that follow on the stream count
-        // their finished blocks on these tickets: start them from zero
-        V.hdr->ticket[0] = 0u;
+        // the validation kernel that follows on the stream counts its
+        // finished blocks on this ticket: start it from zero
         V.hdr->ticket[1] = 0u;
         V.hdr->bad = 0;
     }

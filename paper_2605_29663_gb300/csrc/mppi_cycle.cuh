@@ -3,10 +3,10 @@
 // and the batched persistent kernels (batched.cu):
 //   sample_body    one sample r: rollout, every (step, point) body-frame
 //                  signed distance, per-step minima, J~ (Sec. III-E, IV-C..E)
-//   update_body    one chunk of samples: weights and weighted clipped noise;
-//                  the scene's last chunk sums them, writes U_upd and rolls
-//                  the updated nominal out (Alg. 1 step 3)
-//   validate_body  one (step, point chunk) of the nominal: d_min >= d_safe;
+//   update_body    one chunk of samples: weights and weighted clipped noise
+//                  into a partial slot (Alg. 1 step 3)
+//   validate_body  one (step, point chunk) of the nominal: adds the partial
+//                  slots (U_upd), rolls the nominal out, d_min >= d_safe;
 //                  the scene's last block writes u*, the shifted or reset U
 //                  and the valid flag (Alg. 1 step 4)
 // Blocks never wait for each other: the last block of a phase is found with
@@ -42,8 +42,6 @@ struct SceneView {
     double *Jt;         // K   J~ = J + w_inf I(chi)
     float *wt;          // K   unnormalised weights
     float *part;        // G x (T*nu + 1) partial sums
-    float *Uupd;        // T x nu
-    float4 *nom;        // T   scored nominal states (x, y, cos, sin)
     unsigned *dkey;     // K x T  per-step keys exchanged between horizon parts
     unsigned *tk;       // K      finished horizon parts of each sample
     int upd_chunk, upd_blocks, val_chunks;
@@ -93,8 +91,6 @@ inline size_t scene_scratch_bytes(int K, int T, int parts) {
     b += align_up((size_t)K * sizeof(double), 256);
     b += align_up((size_t)K * sizeof(float), 256);
     b += align_up((size_t)upd_blocks_for(K, T, 3) * (T * 3 + 1) * sizeof(float), 256);
-    b += align_up((size_t)T * 3 * sizeof(float), 256);
-    b += align_up((size_t)T * sizeof(float4), 256);
     if (parts > 1) {
         b += align_up((size_t)K * T * sizeof(unsigned), 256);
         b += align_up((size_t)K * sizeof(unsigned), 256);
@@ -105,8 +101,6 @@ inline void carve_scene(SceneView &V, char *p, int K, int T, int parts) {
     V.Jt = reinterpret_cast<double *>(p); p += align_up((size_t)K * sizeof(double), 256);
     V.wt = reinterpret_cast<float *>(p); p += align_up((size_t)K * sizeof(float), 256);
     V.part = reinterpret_cast<float *>(p); p += align_up((size_t)upd_blocks_for(K, T, 3) * (T * 3 + 1) * sizeof(float), 256);
-    V.Uupd = reinterpret_cast<float *>(p); p += align_up((size_t)T * 3 * sizeof(float), 256);
-    V.nom = reinterpret_cast<float4 *>(p); p += align_up((size_t)T * sizeof(float4), 256);
     V.parts = parts;
     V.dkey = nullptr;
     V.tk = nullptr;
@@ -362,17 +356,12 @@ struct UpdateSmem {
     float tile[kUpdTile];
     float w[256];
     float f[kUpdBlock / 32];
-    float U[EXACT_MAX_HORIZON * 3];
-    float Z;
-    bool last;
 };
 
 // Chunk b of a scene's samples (blockDim == kUpdBlock): it stages its noise
-// rows (contiguous, coalesced, eight loads in flight per thread), forms
-// w_r = exp(-(J~_r - beta)/lambda) and sum_r w_r eps'_r, sum_r w_r into its
-// partial slot.  The scene's last chunk (atomic ticket) adds the partials,
-// writes the normalised weights, the costs and U_upd, and rolls the updated
-// nominal out for validation.
+// rows (contiguous, coalesced, eight loads in flight per thread) before
+// waiting for the sample phase, then forms w_r = exp(-(J~_r - beta)/lambda)
+// and leaves sum_r w_r eps'_r and sum_r w_r in its partial slot.
 __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSmem &sm) {
     const MppiP &P = V.P;
     const int K = P.K, T = P.T, nu = P.nu, TN = T * nu;
@@ -428,40 +417,61 @@ __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSme
         for (int w = 0; w < kUpdBlock / 32; ++w) zb += sm.f[w];
         part[TN] = zb;
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) sm.last = atomicAdd(&V.hdr->ticket[0], 1u) == (unsigned)V.upd_blocks - 1;
     grid_dep_release();
-    __syncthreads();
-    if (!sm.last) return;
-    __threadfence();
+}
 
-    const int G = V.upd_blocks;
-    if (warp == 0) {
-        float zz = 0.f;
-        for (int q = lane; q < G; q += 32) zz += __ldcg(V.part + (size_t)q * (TN + 1) + TN);
-        zz = warp_sum_f(zz);
-        if (lane == 0) sm.Z = zz;
+// ---------------------------------------------------------------- validation
+constexpr int kRedSlices = kBlock / 32;   // slot slices of the partial reduction
+
+struct ValidateSmem {
+    float red[kRedSlices][EXACT_MAX_HORIZON * 3 + 1];
+    float U[EXACT_MAX_HORIZON * 3];
+    float4 pose;
+    float Z;
+    float mn[32];
+    bool last;
+};
+
+// Block (step h, point chunk c) of a scene's validation (blockDim == kBlock).
+// Every block adds the update blocks' partial slots itself (fixed order, so
+// all blocks hold the same U_upd = U + sum_r w_r eps'_r / sum_r w_r), rolls
+// the updated nominal out to its step, and checks the nominal's clearance
+// over its chunk of points.  Block 0 also writes U_upd and the blocks share
+// out the normalised weights and the costs.  The scene's last block (atomic
+// ticket) writes u*, the shifted (last entry repeated) or reset U, the valid
+// flag, and empties beta for the next cycle.
+template <class EV>
+__device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, int h, int c, ValidateSmem &sm) {
+    const MppiP &P = V.P;
+    const int K = P.K, T = P.T, nu = P.nu, TN = T * nu, G = V.upd_blocks;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nblocks = T * V.val_chunks, self = h * V.val_chunks + c;
+    grid_dep_wait();   // the partial slots come from the update phase
+
+    // partial slots: warp w adds slots w, w + 8, ... for every element (and Z)
+    for (int e = lane; e <= TN; e += 32) {
+        float a = 0.f;
+        for (int q = warp; q < G; q += kRedSlices) a += __ldcg(V.part + (size_t)q * (TN + 1) + e);
+        sm.red[warp][e] = a;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float z = 0.f;
+        for (int w = 0; w < kRedSlices; ++w) z += sm.red[w][TN];
+        sm.Z = z;
     }
     __syncthreads();
     const float invZ = 1.f / sm.Z;
-    for (int e = tid; e < TN; e += kUpdBlock) {
-        float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
-        int q = 0;
-        for (; q + 3 < G; q += 4) {
-            t0 += __ldcg(V.part + (size_t)q * (TN + 1) + e);
-            t1 += __ldcg(V.part + (size_t)(q + 1) * (TN + 1) + e);
-            t2 += __ldcg(V.part + (size_t)(q + 2) * (TN + 1) + e);
-            t3 += __ldcg(V.part + (size_t)(q + 3) * (TN + 1) + e);
-        }
-        for (; q < G; ++q) t0 += __ldcg(V.part + (size_t)q * (TN + 1) + e);
-        const float v = U[e] + ((t0 + t1) + (t2 + t3)) * invZ;
+    for (int e = tid; e < TN; e += kBlock) {
+        float a = 0.f;
+        for (int w = 0; w < kRedSlices; ++w) a += sm.red[w][e];
+        const float v = V.U[e] + a * invZ;
         sm.U[e] = v;
-        V.Uupd[e] = v;
-        if (V.U_upd_out) V.U_upd_out[e] = v;
+        if (self == 0 && V.U_upd_out) V.U_upd_out[e] = v;
     }
     if (V.weights || V.costs) {
-        for (int r = tid; r < K; r += kUpdBlock) {
+        const int r0 = (int)(((long long)K * self) / nblocks), r1 = (int)(((long long)K * (self + 1)) / nblocks);
+        for (int r = r0 + tid; r < r1; r += kBlock) {
             if (V.weights) V.weights[r] = __ldcg(V.wt + r) * invZ;
             if (V.costs) V.costs[r] = (float)V.Jt[r];
         }
@@ -469,45 +479,30 @@ __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSme
     __syncthreads();
     if (warp == 0) {
         LaneRollout R;
-        warp_rollout(P, V.state[0], V.state[1], V.state[2], [&](int h, int j) { return clamp_u(P, j, sm.U[h * nu + j]); },
+        warp_rollout(P, V.state[0], V.state[1], V.state[2], [&](int hh, int j) { return clamp_u(P, j, sm.U[hh * nu + j]); },
                      R);
 #pragma unroll
         for (int q = 0; q < kMaxPerLane; ++q) {
-            const int h = lane * R.per + q;
-            if (q < R.per && h < T) {
+            if (q < R.per && lane * R.per + q == h) {
                 float sn, cs;
                 sincosf(R.th[q], &sn, &cs);
-                V.nom[h] = make_float4(R.x[q], R.y[q], cs, sn);
+                sm.pose = make_float4(R.x[q], R.y[q], cs, sn);
             }
         }
     }
-}
-
-// ---------------------------------------------------------------- validation
-struct ValidateSmem {
-    float mn[32];
-    bool last;
-};
-
-// Step h, point chunk c of the updated nominal.  The scene's last block
-// (atomic ticket) writes u*, the shifted (last entry repeated) or reset U,
-// the valid flag, and empties beta for the next cycle.
-template <class EV>
-__device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, int h, int c, ValidateSmem &sm) {
-    const MppiP &P = V.P;
-    grid_dep_wait();   // the nominal comes from the update phase
-    const float4 q = V.nom[h];
+    __syncthreads();
+    const float4 qp = sm.pose;
     const int N = V.N;
     const int npairs = (N + 1) >> 1;
     const int pend = min(npairs, (c + 1) * kValChunkPairs);
     float best = finf();
-    for (int j = c * kValChunkPairs + threadIdx.x; j < pend; j += blockDim.x) {
+    for (int j = c * kValChunkPairs + tid; j < pend; j += kBlock) {
         const int i0 = 2 * j, i1 = min(2 * j + 1, N - 1);
         const float2 o0 = __ldg(V.pts + i0);
         const float2 o1 = __ldg(V.pts + i1);
         float px0, py0, px1, py1;
-        body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
-        body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
+        body_frame(o0.x, o0.y, qp.x, qp.y, qp.z, qp.w, px0, py0);
+        body_frame(o1.x, o1.y, qp.x, qp.y, qp.z, qp.w, px1, py1);
         float k0, k1;
         ev.eval2(px0, py0, px1, py1, k0, k1);
         if (V.mask) {
@@ -517,27 +512,26 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
         best = fmin3(best, k0, k1);
     }
     best = warp_min_f(best);
-    if ((threadIdx.x & 31) == 0) sm.mn[threadIdx.x >> 5] = best;
+    if (lane == 0) sm.mn[warp] = best;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         float b = sm.mn[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fminf(b, sm.mn[w]);
+        for (int w = 1; w < kBlock / 32; ++w) b = fminf(b, sm.mn[w]);
         const float d = b == finf() ? finf() : ev.dist(b);
         if (!(d >= P.d_safe)) atomicExch(&V.hdr->bad, 1);
         __threadfence();
-        sm.last = atomicAdd(&V.hdr->ticket[1], 1u) == (unsigned)(P.T * V.val_chunks) - 1;
+        sm.last = atomicAdd(&V.hdr->ticket[1], 1u) == (unsigned)nblocks - 1;
     }
     __syncthreads();
     if (!sm.last) return;
     __threadfence();
     const int ok = atomicAdd(&V.hdr->bad, 0) == 0;
-    const int T = P.T, nu = P.nu, TN = T * nu;
-    for (int e = threadIdx.x; e < TN; e += blockDim.x) {
-        const float v = __ldcg(V.Uupd + e);
+    for (int e = tid; e < TN; e += kBlock) {
+        const float v = sm.U[e];
         if (e < nu && V.u_star) V.u_star[e] = ok ? v : 0.f;
-        V.U[e] = ok ? (e + nu < TN ? __ldcg(V.Uupd + e + nu) : v) : 0.f;
+        V.U[e] = ok ? (e + nu < TN ? sm.U[e + nu] : v) : 0.f;
     }
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         if (V.valid) *V.valid = ok;
         V.hdr->beta_enc = 0ull;
     }
