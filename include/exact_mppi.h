@@ -153,6 +153,33 @@ int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint
               float *u_star, float *costs, float *weights, int *valid, float *U_upd,
               float *dmin, void *stream);
 
+/* ------------------------------------------------------------------ no allocation
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory (a control loop that must not call
+ * cudaMalloc after start-up, code running during stream capture, a program
+ * whose device memory belongs to another allocator).
+ *
+ * mppi_step_noalloc computes exactly what mppi_step computes (same kernels,
+ * same results) without a context: its scratch is a file-scope device
+ * array of EXACT_NOALLOC_ARENA_BYTES that every GPU loading the library
+ * holds until the process exits.  It allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library call); it clears the parts of the array
+ * that must start at zero with stream-ordered memsets on `stream`.
+ *  - The first call on a device looks the array's device address up (once,
+ *    with that device current); make that first call before any stream
+ *    capture.
+ *  - Every call shares the one array: calls that overlap on the GPU (other
+ *    streams, other host threads) race and give wrong results.
+ *  - Sizes whose scratch does not fit the array return EXACT_ECAPACITY
+ *    (4 MiB holds, e.g., K = 16384 samples with T = 128 and n_u = 3).
+ * Arguments, layouts and the remaining errors are those of mppi_step. */
+#define EXACT_NOALLOC_ARENA_BYTES (4u << 20)
+int mppi_step_noalloc(const float *state, const float *cloud, const uint8_t *mask, int n_points,
+                      const float *waypoints, int n_wp, float *U, const float *noise,
+                      const exact_footprint *fp, const exact_mppi_params *params,
+                      float *u_star, float *costs, float *weights, int *valid, float *U_upd,
+                      float *dmin, void *stream);
+
 /* ------------------------------------------------------------------ batches
  * Many independent scenes (robots) with different K, T, N, footprints and
  * motion models advanced by one control cycle each in a single persistent

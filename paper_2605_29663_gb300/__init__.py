@@ -26,7 +26,8 @@ NU = {DIFF: 2, ACKERMANN: 2, OMNI: 3, SPIN: 1, PARALLEL: 1}
 EXPORTS = ["exact_status_string", "exact_footprint_create", "exact_footprint_destroy",
            "exact_footprint_info", "exact_ctx_create", "exact_ctx_destroy", "exact_ctx_reserve",
            "exact_ctx_get_error", "exact_sdf_batch", "mppi_step", "exact_batch_create", "exact_batch_destroy",
-           "mppi_step_batched", "exact_batch_autotune", "exact_batch_get_tiles", "exact_batch_set_tiles"]
+           "mppi_step_batched", "exact_batch_autotune", "exact_batch_get_tiles", "exact_batch_set_tiles",
+           "mppi_step_noalloc"]
 
 _lock = threading.Lock()
 _lib = None
@@ -81,6 +82,8 @@ def load() -> ctypes.CDLL:
         lib.exact_batch_get_tiles.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
         lib.exact_batch_set_tiles.restype = I
         lib.exact_batch_set_tiles.argtypes = [P, I, I]
+        lib.mppi_step_noalloc.restype = I
+        lib.mppi_step_noalloc.argtypes = [P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
         _lib = lib
         return lib
 

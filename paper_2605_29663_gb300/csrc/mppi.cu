@@ -154,3 +154,24 @@ extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud,
         return EXACT_OK;
     });
 }
+
+namespace exact {
+
+// The three launches of one cycle for a scene whose scratch the caller has
+// already carved (the allocation-free entry point's path; mppi_step keeps
+// its own copy of this sequence).
+int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st) {
+    const size_t smem = (size_t)min(V.N, kStage) * sizeof(float2);
+    return with_footprint(fp, [&](auto fpc) -> int {
+        using FPC = decltype(fpc);
+        const ConstEval<FPC> ev{fpc};
+        mppi_sample_kernel<FPC><<<V.P.K * V.parts, kBlock, smem, st>>>(V, ev);
+        if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
+        if (launch_dependent(mppi_update_kernel, V.upd_blocks, kUpdBlock, 0, st, V) != cudaSuccess) return EXACT_ECUDA;
+        if (launch_dependent(mppi_validate_kernel<FPC>, V.P.T * V.val_chunks, kBlock, 0, st, V, ev) != cudaSuccess)
+            return EXACT_ECUDA;
+        return EXACT_OK;
+    });
+}
+
+}  // namespace exact
