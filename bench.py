@@ -39,6 +39,23 @@ FLOPS_PER_POINT_BOX = 12
 L2_BYTES = 129 * 1024 * 1024
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the headline kernel, from the ncu capture summarised in
+# profiles/sdf_batch_kernel_poly32_16384x8192.md, valid only while the kernel
+# sources hash to the recorded value (reported as null otherwise).
+TRAFFIC = {"sources": ["paper_2605_29663_gb300/csrc/sdf_batch.cu", "paper_2605_29663_gb300/csrc/common.cuh"],
+           "sha256_16": "55dda293bf801ae6", "bytes_per_launch": 350976 + 476276224}
+
+
+def measured_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return TRAFFIC["bytes_per_launch"] if h.hexdigest()[:16] == TRAFFIC["sha256_16"] else None
+
+
 def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
     """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -413,7 +430,7 @@ def run_gpu(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak = fp32_peak_tflops(sm_max)
     achieved = FLOPS_PER_POINT_EDGE * evals / (ms * 1e-3) / 1e12
-    traffic = None
+    traffic = measured_traffic()
     line = {
         "metric": "SDF point-edge evals/s", "value": value, "unit": "point-edge evals/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -425,7 +442,8 @@ def run_gpu(args):
                    "l2": "flushed (2x L2 zero-fill) between timed iterations", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "sdf_batch_kernel<PolyC<32>, true>",
+                     "kernel": "sdf_batch_kernel<PolyC<32>, true, false>",
+                     "algorithmic_bytes_per_launch": N_POSES * N_POINTS * 4 + N_POINTS * 8 + N_POSES * 12,
                      "flops_per_launch": FLOPS_PER_POINT_EDGE * evals,
                      "peak_basis": f"152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_max:.0f} MHz max SM clock "
                                    "(derived; MEASURED_PEAKS.json carries only HBM and bf16 figures)"},
