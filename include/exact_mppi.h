@@ -153,6 +153,60 @@ int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint
               float *u_star, float *costs, float *weights, int *valid, float *U_upd,
               float *dmin, void *stream);
 
+/* ------------------------------------------------------------------ learned proposal
+ * Project extension (the paper has no learned component): a small network
+ * shifts the sampling mean of MPPI; plain MPPI on the same noise remains the
+ * fallback whenever the shifted candidate's best J~ is not lower.
+ *
+ * Network: y = W3 g(W2 g(W1 x + b1) + b2) + b3, g = exact GELU
+ * (z Phi(z)); W1 hidden x d_in, W2 hidden x hidden, W3 d_out x hidden,
+ * row-major.  BF16 x BF16 -> FP32 tensor-core products, FP32 master
+ * parameters and Adam moments (beta1 0.9, beta2 0.999, eps 1e-8), loss =
+ * mean squared error over batch and outputs.  Parameters are exchanged as
+ * one packed FP32 vector [W1, b1, W2, b2, W3, b3] of exact_mlp_num_params
+ * floats.  d_in <= 128, hidden <= 1024, d_out <= 256, batch <= max_batch.
+ * exact_mlp_create allocates device memory; the other calls do not. */
+typedef struct exact_mlp exact_mlp;
+int exact_mlp_create(int d_in, int hidden, int d_out, int max_batch, exact_mlp **out);
+void exact_mlp_destroy(exact_mlp *m);
+long long exact_mlp_num_params(const exact_mlp *m);
+/* host packed parameters in / out (synchronous); set resets Adam */
+int exact_mlp_set_params(exact_mlp *m, const float *host_params);
+int exact_mlp_get_params(const exact_mlp *m, float *host_params);
+/* x device B x d_in -> y device B x d_out */
+int exact_mlp_forward(exact_mlp *m, const float *x, int B, float *y, void *stream);
+/* loss (device 1 float, or NULL) and gradients (device packed vector, or
+ * NULL) of the mean squared error against target (device B x d_out) */
+int exact_mlp_loss_grad(exact_mlp *m, const float *x, const float *target, int B, float *loss, float *grads,
+                        void *stream);
+/* one Adam step with learning rate lr on (x, target); loss as above */
+int exact_mlp_train_step(exact_mlp *m, const float *x, const float *target, int B, float lr, float *loss,
+                         void *stream);
+
+/* Polar nearest-range histogram of B robots: clouds device B x N x 2,
+ * masks device B x N or NULL, poses device B x 3.  Each valid point is moved
+ * into its robot's body frame; bin = floor((atan2(p_y, p_x) + pi) / (2 pi)
+ * nbins) clamped to nbins - 1; out (device B x nbins) = min(r_max, nearest
+ * range in the bin). */
+int exact_polar_hist(const float *clouds, const uint8_t *masks, int B, int N, const float *poses, int nbins,
+                     float r_max, float *out, void *stream);
+/* Network input of B robots, x (device B x (nbins + 7 + 2T)) =
+ * [hist / r_max, goal in the body frame / r_max, previous command (v, w),
+ *  |goal| / r_max, cos and sin of the goal bearing, previous nominal U (T x 2)];
+ * poses B x 3, goals B x 2 (planning frame), prev_cmd B x 2, U_prev B x T x 2. */
+int exact_proposal_features(const float *hist, int nbins, float r_max, const float *poses, const float *goals,
+                            const float *prev_cmd, const float *U_prev, int T, int B, float *x, void *stream);
+/* U_prop = U_prev + shift, U_plain = U_prev (n floats each, device). */
+int exact_proposal_prepare(const float *U_prev, const float *shift, long long n, float *U_prop, float *U_plain,
+                           void *stream);
+/* Per robot b: keep the proposal candidate when min_r costs_prop[b] <
+ * min_r costs_plain[b] (device B x K each): copy its nominal (B x T x nu)
+ * and command (B x nu) to U_out / u_out; chose_prop (device B, or NULL)
+ * records the choice. */
+int exact_proposal_select(const float *costs_prop, const float *costs_plain, int B, int K, const float *U_prop,
+                          const float *U_plain, const float *u_prop, const float *u_plain, int T, int nu,
+                          float *U_out, float *u_out, int *chose_prop, void *stream);
+
 /* ------------------------------------------------------------------ no allocation
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory (a control loop that must not call

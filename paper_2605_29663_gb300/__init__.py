@@ -15,7 +15,8 @@ import threading
 
 from . import build as _build
 
-__all__ = ["load", "Footprint", "Context", "MppiParams", "sdf_batch", "mppi_step", "Batch", "ExactError",
+__all__ = ["load", "Footprint", "Context", "MppiParams", "sdf_batch", "mppi_step", "Batch", "ExactError", "MLP",
+           "polar_hist", "proposal_features", "proposal_prepare", "proposal_select",
            "POLYGON", "RECTS", "DIFF", "ACKERMANN", "OMNI", "SPIN", "PARALLEL", "NU", "EXPORTS"]
 
 POLYGON, RECTS = 0, 1
@@ -27,7 +28,10 @@ EXPORTS = ["exact_status_string", "exact_footprint_create", "exact_footprint_des
            "exact_footprint_info", "exact_ctx_create", "exact_ctx_destroy", "exact_ctx_reserve",
            "exact_ctx_get_error", "exact_sdf_batch", "mppi_step", "exact_batch_create", "exact_batch_destroy",
            "mppi_step_batched", "exact_batch_autotune", "exact_batch_get_tiles", "exact_batch_set_tiles",
-           "mppi_step_noalloc"]
+           "mppi_step_noalloc", "exact_mlp_create", "exact_mlp_destroy", "exact_mlp_num_params",
+           "exact_mlp_set_params", "exact_mlp_get_params", "exact_mlp_forward", "exact_mlp_loss_grad",
+           "exact_mlp_train_step", "exact_polar_hist", "exact_proposal_features", "exact_proposal_prepare",
+           "exact_proposal_select"]
 
 _lock = threading.Lock()
 _lib = None
@@ -84,6 +88,31 @@ def load() -> ctypes.CDLL:
         lib.exact_batch_set_tiles.argtypes = [P, I, I]
         lib.mppi_step_noalloc.restype = I
         lib.mppi_step_noalloc.argtypes = [P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
+        F, LL = ctypes.c_float, ctypes.c_longlong
+        lib.exact_mlp_create.restype = I
+        lib.exact_mlp_create.argtypes = [I, I, I, I, ctypes.POINTER(P)]
+        lib.exact_mlp_destroy.restype = V
+        lib.exact_mlp_destroy.argtypes = [P]
+        lib.exact_mlp_num_params.restype = LL
+        lib.exact_mlp_num_params.argtypes = [P]
+        lib.exact_mlp_set_params.restype = I
+        lib.exact_mlp_set_params.argtypes = [P, P]
+        lib.exact_mlp_get_params.restype = I
+        lib.exact_mlp_get_params.argtypes = [P, P]
+        lib.exact_mlp_forward.restype = I
+        lib.exact_mlp_forward.argtypes = [P, P, I, P, P]
+        lib.exact_mlp_loss_grad.restype = I
+        lib.exact_mlp_loss_grad.argtypes = [P, P, P, I, P, P, P]
+        lib.exact_mlp_train_step.restype = I
+        lib.exact_mlp_train_step.argtypes = [P, P, P, I, F, P, P]
+        lib.exact_polar_hist.restype = I
+        lib.exact_polar_hist.argtypes = [P, P, I, I, P, I, F, P, P]
+        lib.exact_proposal_features.restype = I
+        lib.exact_proposal_features.argtypes = [P, I, F, P, P, P, P, I, I, P, P]
+        lib.exact_proposal_prepare.restype = I
+        lib.exact_proposal_prepare.argtypes = [P, P, LL, P, P, P]
+        lib.exact_proposal_select.restype = I
+        lib.exact_proposal_select.argtypes = [P, P, I, I, P, P, P, P, I, I, P, P, P, P]
         _lib = lib
         return lib
 
@@ -385,3 +414,134 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class MLP:
+    """Proposal network on the tensor cores (see exact_mlp_* in the C header).
+    Parameters are exchanged as one packed float32 vector
+    [W1 (H x D), b1, W2 (H x H), b2, W3 (O x H), b3]."""
+
+    def __init__(self, d_in: int, hidden: int, d_out: int, max_batch: int):
+        h = ctypes.c_void_p()
+        _check(load().exact_mlp_create(d_in, hidden, d_out, max_batch, ctypes.byref(h)), "exact_mlp_create")
+        self._h = h
+        self.d_in, self.hidden, self.d_out, self.max_batch = d_in, hidden, d_out, max_batch
+        self.num_params = int(load().exact_mlp_num_params(h))
+
+    def shapes(self):
+        D, H, O = self.d_in, self.hidden, self.d_out
+        return [(H, D), (H,), (H, H), (H,), (O, H), (O,)]
+
+    def init_params(self, seed: int = 0):
+        """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and biases (seeded)."""
+        import numpy as np
+        g = np.random.default_rng(seed)
+        parts = []
+        for shp in self.shapes():
+            fan_in = shp[1] if len(shp) == 2 else (self.d_in if len(parts) == 1 else self.hidden)
+            parts.append(g.uniform(-1.0, 1.0, size=shp) / np.sqrt(fan_in))
+        self.set_params(np.concatenate([p.reshape(-1) for p in parts]))
+
+    def set_params(self, flat):
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32).reshape(-1))
+        if a.size != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters, got {a.size}")
+        _check(load().exact_mlp_set_params(self._h, a.ctypes.data), "exact_mlp_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.num_params, dtype=np.float32)
+        _check(load().exact_mlp_get_params(self._h, a.ctypes.data), "exact_mlp_get_params")
+        return a
+
+    def unpack(self, flat):
+        out, k = [], 0
+        for shp in self.shapes():
+            n = 1
+            for s in shp:
+                n *= s
+            out.append(flat[k:k + n].reshape(shp))
+            k += n
+        return out
+
+    def forward(self, x, out=None, stream=None):
+        torch = _torch()
+        x = _dev(x, "x", torch.float32)
+        B = x.shape[0]
+        y = out if out is not None else torch.empty((B, self.d_out), dtype=torch.float32, device=x.device)
+        _check(load().exact_mlp_forward(self._h, _ptr(x), B, _ptr(y), _stream(stream)), "exact_mlp_forward")
+        return y
+
+    def loss_grad(self, x, target, stream=None):
+        torch = _torch()
+        x = _dev(x, "x", torch.float32)
+        target = _dev(target, "target", torch.float32)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        grads = torch.empty(self.num_params, dtype=torch.float32, device=x.device)
+        _check(load().exact_mlp_loss_grad(self._h, _ptr(x), _ptr(target), x.shape[0], _ptr(loss), _ptr(grads),
+                                          _stream(stream)), "exact_mlp_loss_grad")
+        return loss, grads
+
+    def train_step(self, x, target, lr: float, loss=None, stream=None):
+        torch = _torch()
+        x = _dev(x, "x", torch.float32)
+        target = _dev(target, "target", torch.float32)
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check(load().exact_mlp_train_step(self._h, _ptr(x), _ptr(target), x.shape[0], float(lr), _ptr(loss),
+                                           _stream(stream)), "exact_mlp_train_step")
+        return loss
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().exact_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def polar_hist(clouds, poses, nbins: int = 64, r_max: float = 10.0, masks=None, out=None, stream=None):
+    """Nearest range per angular bin of each robot's points (B x N x 2 clouds, B x 3 poses)."""
+    torch = _torch()
+    clouds = _dev(clouds, "clouds", torch.float32)
+    poses = _dev(poses, "poses", torch.float32)
+    B, N = clouds.shape[0], clouds.shape[1]
+    if masks is not None:
+        masks = _dev(masks, "masks", torch.uint8, (B, N))
+    o = out if out is not None else torch.empty((B, nbins), dtype=torch.float32, device=poses.device)
+    _check(load().exact_polar_hist(_ptr(clouds), _ptr(masks), B, N, _ptr(poses), nbins, float(r_max), _ptr(o),
+                                   _stream(stream)), "exact_polar_hist")
+    return o
+
+
+def proposal_features(hist, poses, goals, prev_cmd, U_prev, r_max: float = 10.0, out=None, stream=None):
+    torch = _torch()
+    B, nbins = hist.shape
+    T = U_prev.shape[1]
+    o = out if out is not None else torch.empty((B, nbins + 7 + 2 * T), dtype=torch.float32, device=hist.device)
+    _check(load().exact_proposal_features(_ptr(_dev(hist, "hist", torch.float32)), nbins, float(r_max),
+                                          _ptr(_dev(poses, "poses", torch.float32)),
+                                          _ptr(_dev(goals, "goals", torch.float32)),
+                                          _ptr(_dev(prev_cmd, "prev_cmd", torch.float32)),
+                                          _ptr(_dev(U_prev, "U_prev", torch.float32)), T, B, _ptr(o), _stream(stream)),
+           "exact_proposal_features")
+    return o
+
+
+def proposal_prepare(U_prev, shift, U_prop, U_plain, stream=None):
+    _check(load().exact_proposal_prepare(_ptr(U_prev), _ptr(shift), U_prev.numel(), _ptr(U_prop), _ptr(U_plain),
+                                         _stream(stream)), "exact_proposal_prepare")
+
+
+def proposal_select(costs_prop, costs_plain, U_prop, U_plain, u_prop, u_plain, U_out, u_out, chose=None,
+                    stream=None):
+    B, K = costs_prop.shape
+    T, nu = U_prop.shape[1], U_prop.shape[2]
+    _check(load().exact_proposal_select(_ptr(costs_prop), _ptr(costs_plain), B, K, _ptr(U_prop), _ptr(U_plain),
+                                        _ptr(u_prop), _ptr(u_plain), T, nu, _ptr(U_out), _ptr(u_out), _ptr(chose),
+                                        _stream(stream)), "exact_proposal_select")

@@ -25,7 +25,8 @@ def lib():
 def _declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?(?:(?:unsigned|long|short)\s+)*[A-Za-z_][A-Za-z0-9_]*(?:\s+|\s*\*+\s*)"
+                       r"([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
