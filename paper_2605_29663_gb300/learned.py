@@ -14,10 +14,13 @@ simulates the world (moving obstacles, executing the chosen command) on the
 host and orchestrates the calls.
 
 World (one robot per environment): diff-drive robot with the concave L
-footprint, goal 8-10 m ahead, 25 static boxes (0.3-1.0 m) and 40 discs of
-radius 0.3 m moving at 0.5 m/s (bouncing inside the arena), all sampled as
-points every 0.05 m; the robot senses the points within 6 m, fitted to a
-budget of N = 2048 (uniform subsample, or zero padding plus mask).
+footprint, goal 8-10 m ahead in a (G + 24) x 30 m arena, 8 static boxes
+(0.3-1.0 m) between start and goal and 40 discs of radius 0.3 m moving at
+0.5 m/s (bouncing inside
+the arena, starting at least 2.5 m from the robot), all sampled as points
+every 0.05 m; the robot senses the points within 6 m, fitted to a budget of
+N = 2048 (uniform subsample, or zero padding plus mask).  An episode ends at
+the goal (0.5 m), at a collision (exact clearance < 0) or after 250 steps.
 """
 from __future__ import annotations
 
@@ -42,7 +45,7 @@ R_SENSE = 6.0
 DT = 0.1
 SIGMA = (0.3, 0.6)
 U_LO, U_HI = (-1.0, -1.5), (1.5, 1.5)
-GOAL_TOL = 0.3
+GOAL_TOL = 0.5
 D_IN = NBINS + 7 + 2 * T_H          # 111
 
 
@@ -54,8 +57,9 @@ def mppi_params(K: int) -> dict:
 class World:
     """n independent seeded environments (host-side simulation)."""
 
-    def __init__(self, n: int, seed: int, max_steps: int = 200):
+    def __init__(self, n: int, seed: int, max_steps: int = 250, n_boxes: int = 8, n_discs: int = 40):
         self.n = n
+        self.n_boxes, self.n_discs = n_boxes, n_discs
         self.max_steps = max_steps
         self.seed = seed
         self.next_scene = 0
@@ -64,8 +68,8 @@ class World:
         self.prev_cmd = np.zeros((n, 2))
         self.steps = np.zeros(n, dtype=int)
         self.static = [None] * n
-        self.dc = np.zeros((n, 40, 2))
-        self.dv = np.zeros((n, 40, 2))
+        self.dc = np.zeros((n, n_discs, 2))
+        self.dv = np.zeros((n, n_discs, 2))
         self.lo = np.zeros((n, 2))
         self.hi = np.zeros((n, 2))
         ang = np.arange(38) * (2 * math.pi / 38)
@@ -81,20 +85,20 @@ class World:
         self.pose[i] = (0.0, 0.0, 0.0)
         self.prev_cmd[i] = 0.0
         self.steps[i] = 0
-        self.lo[i] = (-2.0, -5.0)
-        self.hi[i] = (G + 2.0, 5.0)
+        self.lo[i] = (-12.0, -15.0)
+        self.hi[i] = (G + 12.0, 15.0)
         boxes = []
-        while len(boxes) < 25:
-            c = np.array([g.uniform(1.5, G - 0.5), g.uniform(-4.5, 4.5)])
-            if np.hypot(*c) < 1.6 or np.hypot(*(c - self.goal[i])) < 1.2:
+        while len(boxes) < self.n_boxes:
+            c = np.array([g.uniform(2.0, G - 0.5), g.uniform(-6.0, 6.0)])
+            if np.hypot(*c) < 2.0 or np.hypot(*(c - self.goal[i])) < 1.5:
                 continue
             w, h = g.uniform(0.3, 1.0, 2)
             boxes.append(synth.box_edge_points(c[0], c[1], w, h, 0.05))
-        self.static[i] = np.concatenate(boxes)
+        self.static[i] = np.concatenate(boxes) if boxes else np.zeros((0, 2))
         k = 0
-        while k < 40:
+        while k < self.n_discs:
             c = g.uniform(self.lo[i], self.hi[i])
-            if np.hypot(*c) < 2.0:
+            if np.hypot(*c) < 2.5:
                 continue
             self.dc[i, k] = c
             a = g.uniform(-math.pi, math.pi)
@@ -314,14 +318,14 @@ def train(torch, mlp: MLP, X, Y, epochs: int, batch: int, lr: float, seed: int, 
 
 
 def evaluate(torch, dev, method: str, K: int, n_episodes: int, seed: int, mlp: MLP | None = None,
-             max_steps: int = 200, log=print) -> dict:
+             max_steps: int = 250, log=print, world_kw=None) -> dict:
     """Closed-loop episodes on seeded held-out worlds (the same worlds for
     every method).  Final trajectory cost = sum over executed steps of
     w_goal |p - g| + w_ctrl |u|^2 + phi_obs(d), d the exact clearance of the
     executed pose; after a collision the robot stays put and every remaining
     step adds w_coll + the goal term."""
     fp = Footprint.polygon(synth.l_footprint())
-    world = World(n_episodes, seed, max_steps)
+    world = World(n_episodes, seed, max_steps, **(world_kw or {}))
     if method == "plain":
         ctl = PlainController(torch, dev, n_episodes, K, fp)
     else:
@@ -365,14 +369,17 @@ def evaluate(torch, dev, method: str, K: int, n_episodes: int, seed: int, mlp: M
     rem = max_steps - (step + 1)
     cost += np.where(collided, (p["w_coll"] + p["w_goal"] * world.goal_dist()) * rem, 0.0)
     ci = 1.96 * cost.std(ddof=1) / math.sqrt(n_episodes)
+    progress = np.hypot(world.goal[:, 0], world.goal[:, 1]) - world.goal_dist()
     res = {"method": method, "K": K, "episodes": n_episodes, "cost_mean": float(cost.mean()), "cost_ci95": float(ci),
+           "progress_mean_m": float(progress.mean()),
            "success_rate": float(success.mean()), "collision_rate": float(collided.mean()),
            "steps_to_goal_mean": float(t_goal[success].mean()) if success.any() else None,
            "gpu_ms_per_step": gpu_ms / (step + 1), "costs": cost.tolist()}
     if chose:
         res["proposal_chosen_frac"] = float(np.mean(chose))
     if log:
-        log(f"{method} K={K}: cost {res['cost_mean']:.1f} +- {ci:.1f}, success {res['success_rate']:.2f}, "
+        log(f"{method} K={K}: cost {res['cost_mean']:.1f} +- {ci:.1f}, progress {res['progress_mean_m']:.2f} m, "
+            f"success {res['success_rate']:.2f}, "
             f"collisions {res['collision_rate']:.2f}, {res['gpu_ms_per_step']:.2f} ms/step")
     return res
 
