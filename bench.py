@@ -211,7 +211,7 @@ def time_graph(torch, fn, iters: int, warm: int = 3):
     return e0.elapsed_time(e1) / iters
 
 
-def mppi_extra(torch, ex, dev):
+def mppi_extra(torch, ex, dev, cpu: bool = True):
     import synth
     out = {}
     ctx = ex.Context()
@@ -239,8 +239,26 @@ def mppi_extra(torch, ex, dev):
         out[name] = {"steps_per_s": 1e3 / ms, "us_per_step": 1e3 * ms, "K": p["K"], "T": p["T"], "N": N,
                      "footprint": ("polygon" if s["kind"] == synth.POLYGON else "rects") + f"x{s['fp'].shape[0]}",
                      "evals_per_step": per_step, "counted_tflops": flops / (ms * 1e-3) / 1e12,
-                     "launches_per_step": 3, "timing": "CUDA graph replay, events, inputs L2-resident"}
+                     "launches_per_step": 3, "timing": "CUDA graph replay, events, inputs L2-resident",
+                     "cpu_oracle": oracle_mppi_sample(s) if cpu else None}
     return out
+
+
+def oracle_mppi_sample(s, budget_s: float = 3.0) -> dict:
+    """The FP64 oracle's full control cycle on the same scene, repeated until
+    about budget_s seconds have passed (at least once)."""
+    import oracle
+    oracle.build()
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.mppi_step(s["params"], s["q0"], s["cloud"], s["waypoints"], s["U"], s["eps"], s["kind"], s["fp"],
+                         mask=s["mask"])
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    return {"steps_per_s": n / dt, "ms_per_step": 1e3 * dt / n, "steps": n, "cores": oracle.max_threads(),
+            "kind": "oracle", "sample": f"{n} full cycles of the same scene, float64, OpenMP over samples"}
 
 
 def batched_extra(torch, ex, dev, steps=3, tune=True):
@@ -454,10 +472,10 @@ def run_gpu(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
-    if not args.no_cpu:
+    if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
-    if not args.no_extra:
-        line["extra"] = mppi_extra(torch, ex, dev)
+    if not args.no_extra and world == 1:
+        line["extra"] = mppi_extra(torch, ex, dev, cpu=not args.no_cpu)
         line["extra"]["batched64"] = batched_extra(torch, ex, dev)
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -340,6 +340,7 @@ def evaluate(torch, dev, method: str, K: int, n_episodes: int, seed: int, mlp: M
     t_goal = np.full(n_episodes, max_steps)
     cost = np.zeros(n_episodes)
     chose = []
+    best_gap = []      # per active step: min J~ of the plain candidate - min J~ of the kept one
     gpu_ms = 0.0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for step in range(max_steps):
@@ -350,8 +351,11 @@ def evaluate(torch, dev, method: str, K: int, n_episodes: int, seed: int, mlp: M
         torch.cuda.synchronize()
         gpu_ms += e0.elapsed_time(e1)
         u = out[0].cpu().numpy().astype(np.float64)
-        if method != "plain":
-            chose.append(ctl.chose.cpu().numpy()[active].mean() if active.any() else 0.0)
+        if method != "plain" and active.any():
+            chose.append(ctl.chose.cpu().numpy()[active].mean())
+            mp = out[1].min(1).values.cpu().numpy()[active]
+            mq = out[2].min(1).values.cpu().numpy()[active]
+            best_gap.append(float(np.mean(mq - np.minimum(mp, mq))))
         u[~active] = 0.0
         world.move(u)
         d = executed_clearance(world, fp, torch, dev)
@@ -377,6 +381,7 @@ def evaluate(torch, dev, method: str, K: int, n_episodes: int, seed: int, mlp: M
            "gpu_ms_per_step": gpu_ms / (step + 1), "costs": cost.tolist()}
     if chose:
         res["proposal_chosen_frac"] = float(np.mean(chose))
+        res["best_cost_gain_mean"] = float(np.mean(best_gap))
     if log:
         log(f"{method} K={K}: cost {res['cost_mean']:.1f} +- {ci:.1f}, progress {res['progress_mean_m']:.2f} m, "
             f"success {res['success_rate']:.2f}, "
