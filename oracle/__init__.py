@@ -66,7 +66,9 @@ def lib():
             _lib.ox_rollout.argtypes = [I, D, P, P, I, I, D, P]
             _lib.ox_mppi_step.restype = I
             _lib.ox_mppi_step.argtypes = [P, P, P, P, I, P, I, P, P, I, P, I,
-                                          P, P, P, P, P, P, P, P, D]
+                                          P, P, P, P, P, P, P, P, P, D]
+            _lib.ox_hybrid_select.restype = I
+            _lib.ox_hybrid_select.argtypes = [I, P, P, D, I, P, P, P]
             _lib.ox_polar_hist.argtypes = [P, P, I, D, D, D, I, D, P]
             _lib.ox_mlp_forward.argtypes = [P] * 6 + [I, I, I, P, I, P]
             _lib.ox_mlp_loss_grad.restype = D
@@ -185,7 +187,8 @@ def mppi_step(params: dict, q0, cloud, waypoints, U, eps, kind: int, fp, mask=No
               near_tol: float = 1e-5) -> dict:
     """One control cycle of Algorithm 1.  Returns a dict with U (shifted or reset),
     U_upd (updated nominal), u_star, costs (J~), weights (omega), valid,
-    dmin (K x T), dmin_nom (T) and n_near (threshold-adjacent d_min count)."""
+    dmin (K x T), dmin_nom (T), J_nom (cost of the updated nominal) and n_near
+    (threshold-adjacent d_min count)."""
     P = make_params(params)
     K, T, nu = P.K, P.T, P.nu
     pts = _f64(cloud, (-1, 2))
@@ -203,6 +206,7 @@ def mppi_step(params: dict, q0, cloud, waypoints, U, eps, kind: int, fp, mask=No
     U_upd = np.empty((T, nu))
     dmin = np.empty((K, T))
     dmin_nom = np.empty(T)
+    J_nom = ctypes.c_double(0.0)
     n_near = ctypes.c_int(0)
     rc = lib().ox_mppi_step(ctypes.byref(P), q.ctypes.data, pts.ctypes.data,
                             None if m is None else m.ctypes.data, N,
@@ -210,11 +214,48 @@ def mppi_step(params: dict, q0, cloud, waypoints, U, eps, kind: int, fp, mask=No
                             kind, f.ctypes.data, f.shape[0],
                             u_star.ctypes.data, costs.ctypes.data, weights.ctypes.data,
                             ctypes.addressof(valid), U_upd.ctypes.data, dmin.ctypes.data,
-                            dmin_nom.ctypes.data, ctypes.addressof(n_near), near_tol)
+                            dmin_nom.ctypes.data, ctypes.addressof(J_nom), ctypes.addressof(n_near), near_tol)
     if rc != 0:
         raise ValueError("oracle mppi_step rejected its arguments")
     return dict(U=Uio, U_upd=U_upd, u_star=u_star, costs=costs, weights=weights,
-                valid=bool(valid.value), dmin=dmin, dmin_nom=dmin_nom, n_near=int(n_near.value))
+                valid=bool(valid.value), dmin=dmin, dmin_nom=dmin_nom, J_nom=float(J_nom.value),
+                n_near=int(n_near.value))
+
+
+def hybrid_select(J, valid, lambda_switch: float, tau_max: int, m_prev: int, tau: int):
+    """Mode selection of Algorithm 2 (steps 1-2) from per-mode nominal costs and
+    validation flags.  Returns (m_star or -1 for a safe stop, m_prev', tau', Jbar)."""
+    Jd = _f64(J).reshape(-1)
+    M = Jd.size
+    v = np.ascontiguousarray(np.asarray(valid, dtype=np.int32).reshape(M))
+    mp = ctypes.c_int(int(m_prev))
+    tc = ctypes.c_int(int(tau))
+    Jbar = np.empty(M)
+    ms = lib().ox_hybrid_select(M, Jd.ctypes.data, v.ctypes.data, float(lambda_switch), int(tau_max),
+                                ctypes.addressof(mp), ctypes.addressof(tc), Jbar.ctypes.data)
+    return int(ms), int(mp.value), int(tc.value), Jbar
+
+
+def hybrid_step(modes, hp: dict, m_prev: int, tau: int, near_tol: float = 1e-5) -> dict:
+    """One hybrid-mode cycle (Algorithm 2, steps 1-2): Algorithm 1 per mode
+    (each mode dict holds params, q0, cloud, mask, waypoints, U, eps, kind, fp;
+    its U is advanced in place), then the selection.  u is the chosen mode's
+    first command (zero padded to 3; zero on a safe stop)."""
+    outs = []
+    for md in modes:
+        o = mppi_step(md["params"], md["q0"], md["cloud"], md["waypoints"], md["U"], md["eps"], md["kind"],
+                      md["fp"], mask=md.get("mask"), near_tol=near_tol)
+        md["U"] = o["U"]
+        outs.append(o)
+    J = [o["J_nom"] for o in outs]
+    valid = [o["valid"] for o in outs]
+    ms, mp, tc, Jbar = hybrid_select(J, valid, hp["lambda_switch"], hp["cool_max"], m_prev, tau)
+    u = np.zeros(3)
+    if ms >= 0:
+        us = outs[ms]["u_star"]
+        u[:us.size] = us
+    return dict(mode=mp, tau=tc, stopped=ms < 0, u=u, Jbar=Jbar, J=np.array(J), valid=np.array(valid),
+                modes=outs)
 
 
 def goal_dist(x, y, waypoints) -> float:

@@ -311,16 +311,18 @@ static double clamp_dim(const ox_params *P, int j, double u) {
  *        U (T x nu), eps (K x T x nu), footprint.
  *   out: U (T x nu, shifted or reset), u_star (nu), costs J~ (K), weights
  *        omega (K), *valid, U_upd (updated nominal before shift/reset),
- *        dmin (K x T) and dmin_nom (T) when non-NULL, *n_near = number of
- *        (sample, step) and nominal steps whose d_min lies within near_tol of
- *        0 or d_safe (where FP32 and FP64 may legitimately disagree).
+ *        dmin (K x T) and dmin_nom (T) when non-NULL, *J_nom = the cost J of
+ *        the updated nominal (scored like a sample, zero noise) when non-NULL,
+ *        *n_near = number of (sample, step) and nominal steps whose d_min lies
+ *        within near_tol of 0 or d_safe (where FP32 and FP64 may legitimately
+ *        disagree).
  * Returns 0, or -1 on bad arguments / allocation failure. */
 int ox_mppi_step(const ox_params *P, const double q0[3],
                  const double *cloud, const uint8_t *mask, int N,
                  const double *wp, int W, double *U, const double *eps,
                  int kind, const double *fp, int n,
                  double *u_star, double *costs, double *weights, int *valid,
-                 double *U_upd, double *dmin, double *dmin_nom,
+                 double *U_upd, double *dmin, double *dmin_nom, double *J_nom,
                  int *n_near, double near_tol) {
     int K = P->K, T = P->T, nu = P->nu;
     if (K <= 0 || T <= 0 || nu != ox_model_nu(P->model) || !(P->lambda > 0.0)) return -1;
@@ -378,7 +380,8 @@ int ox_mppi_step(const ox_params *P, const double q0[3],
     for (int h = 0; h < T; ++h)
         for (int j = 0; j < nu; ++j) u[h * nu + j] = clamp_dim(P, j, U[h * nu + j]);
     int chi_nom = 0, nn = 0;
-    (void)sequence_cost(P, q0, u, cloud, mask, N, wp, W, kind, fp, n, st, dn, &chi_nom, &nn, near_tol);
+    double Jn = sequence_cost(P, q0, u, cloud, mask, N, wp, W, kind, fp, n, st, dn, &chi_nom, &nn, near_tol);
+    if (J_nom) *J_nom = Jn;
     int ok = 1;
     for (int h = 0; h < T; ++h) if (!(dn[h] >= P->d_safe)) ok = 0;
     near_total += nn;
@@ -398,6 +401,36 @@ int ox_mppi_step(const ox_params *P, const double q0[3],
     if (n_near) *n_near = near_total;
     free(u); free(st); free(dn); free(epsc); free(Jt);
     return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Hybrid-mode selection (Sec. III-F, Algorithm 2, steps 1 and 2).  Every mode
+ * m of the set has already run its own Algorithm 1 cycle, giving the cost
+ * J[m] of its updated nominal and its validation flag valid[m].
+ *   Jbar_m = J_m + lambda_switch * I(m != m_prev) if valid, else +inf;
+ *   all +inf          -> safe stop: returns -1, *m_prev and *tau unchanged;
+ *   m* = argmin Jbar  (the lowest mode index among equal values);
+ *   tau > 0 and m* != m_prev -> m* = m_prev (cooldown; only when m_prev is a
+ *                        mode of the set: m_prev = -1 means "none yet");
+ *   tau = tau_max if m* != m_prev else max(tau - 1, 0);  m_prev = m*.
+ * Jbar (M) receives the augmented costs when non-NULL.  Returns m*.
+ * ------------------------------------------------------------------------- */
+int ox_hybrid_select(int M, const double *J, const int *valid, double lambda_switch, int tau_max,
+                     int *m_prev, int *tau, double *Jbar) {
+    int best = -1;
+    double best_J = INFINITY;
+    for (int m = 0; m < M; ++m) {
+        double jb = valid[m] ? J[m] + (m != *m_prev ? lambda_switch : 0.0) : INFINITY;
+        if (Jbar) Jbar[m] = jb;
+        if (jb < best_J) { best_J = jb; best = m; }
+    }
+    if (best < 0) return -1;
+    int ms = best;
+    if (*tau > 0 && ms != *m_prev && *m_prev >= 0 && *m_prev < M) ms = *m_prev;
+    if (ms != *m_prev) *tau = tau_max;
+    else *tau = *tau > 0 ? *tau - 1 : 0;
+    *m_prev = ms;
+    return ms;
 }
 
 /* ---------------------------------------------------------------------------
