@@ -244,6 +244,41 @@ def mppi_extra(torch, ex, dev, cpu: bool = True):
     return out
 
 
+def hybrid_extra(torch, ex, dev, cpu: bool = True):
+    """Hybrid-mode cycle (three modes of one robot: Ackermann, parallel, spin;
+    K = 1024 each, T = 20, N = 2048, 8-vertex footprint): the batched launch set
+    plus the selection kernel, replayed from a CUDA graph."""
+    import synth
+    modes = synth.hybrid(0)
+    fp = ex.Footprint(modes[0]["kind"], modes[0]["fp"])
+    shared = dict(state=torch.from_numpy(modes[0]["q0"]).to(dev), cloud=torch.from_numpy(modes[0]["cloud"]).to(dev),
+                  waypoints=torch.from_numpy(modes[0]["waypoints"]).to(dev),
+                  mask=None if modes[0]["mask"] is None else torch.from_numpy(modes[0]["mask"]).to(dev))
+    devs = [dict(shared, U=torch.from_numpy(m["U"]).to(dev), noise=torch.from_numpy(m["eps"]).to(dev), fp=fp,
+                 params=m["params"]) for m in modes]
+    h = ex.Hybrid(devs, lambda_switch=2.0, cool_max=3)
+    h.step()
+    torch.cuda.synchronize()
+    ms = time_graph(torch, h.step, 300)
+    p0 = modes[0]["params"]
+    N = modes[0]["cloud"].shape[0]
+    E = modes[0]["fp"].shape[0]
+    evals = sum(m["params"]["K"] * m["params"]["T"] for m in modes) * N * E
+    out = {"modes": ["ackermann", "parallel", "spin"], "K_per_mode": p0["K"], "T": p0["T"], "N": N,
+           "footprint": f"polygonx{E}", "us_per_cycle": 1e3 * ms, "cycles_per_s": 1e3 / ms,
+           "evals_per_cycle": evals, "counted_tflops": FLOPS_PER_POINT_EDGE * evals / (ms * 1e-3) / 1e12,
+           "launches_per_cycle": 4, "timing": "CUDA graph replay (memset + 3 batched kernels + selection), events"}
+    if cpu:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.hybrid_step([dict(m) for m in modes], dict(lambda_switch=2.0, cool_max=3), -1, 0)
+        dt = time.perf_counter() - t0
+        out["cpu_oracle"] = {"ms_per_cycle": 1e3 * dt, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": "1 full hybrid cycle (3 modes), float64, OpenMP over samples"}
+    return out
+
+
 def oracle_mppi_sample(s, budget_s: float = 3.0) -> dict:
     """The FP64 oracle's full control cycle on the same scene, repeated until
     about budget_s seconds have passed (at least once)."""
@@ -477,6 +512,7 @@ def run_gpu(args):
     if not args.no_extra and world == 1:
         line["extra"] = mppi_extra(torch, ex, dev, cpu=not args.no_cpu)
         line["extra"]["batched64"] = batched_extra(torch, ex, dev)
+        line["extra"]["hybrid3"] = hybrid_extra(torch, ex, dev, cpu=not args.no_cpu)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -259,6 +259,8 @@ typedef struct {
     int *valid;                  /* device, 1, or NULL */
     float *U_upd;                /* device, T x n_u, or NULL */
     float *dmin;                 /* device, K x T, or NULL */
+    float *nom_cost;             /* device, 1, or NULL: cost J of the updated nominal,
+                                    scored like a sample (the J_m of Algorithm 2) */
 } exact_scene;
 
 /* A batch plan: validates the scenes, uploads a device scene table, the
@@ -288,6 +290,50 @@ int exact_batch_autotune(exact_batch *batch, int iters, char *json_out, int json
 int exact_batch_get_tiles(const exact_batch *batch, int *threads, int *pairs_per_lane);
 /* Set the tile shape (threads in {64, 128, 256, 512}, pairs_per_lane in 1..8). */
 int exact_batch_set_tiles(exact_batch *batch, int threads, int pairs_per_lane);
+
+/* ------------------------------------------------------------------ hybrid modes
+ * Hybrid-mode EXACT-MPPI (Sec. III-F, Algorithm 2, steps 1-2) for platforms
+ * with several non-skidding motion modes (e.g. Ackermann, parallel, spin).
+ * Each mode m is a scene (exact_scene) of the same robot: it shares the
+ * caller's state, cloud and footprint as the caller chooses and has its own
+ * motion model, nominal sequence U_m, noise and parameters.  One step runs
+ * Algorithm 1 for every mode (one batched launch set, as mppi_step_batched:
+ * each U_m is updated and shifted or reset), then one selection kernel:
+ *   Jbar_m = J_m + lambda_switch * I(m != m_prev) if mode m's nominal passed
+ *            validation, else +inf, J_m = cost of mode m's updated nominal;
+ *   all +inf: safe stop (zero command, m_prev and tau_cool unchanged);
+ *   m* = argmin Jbar_m (lowest mode index on ties); while tau_cool > 0 a
+ *   switch away from m_prev is refused (m* = m_prev; m_prev = -1 means no
+ *   mode yet and is never kept);
+ *   tau_cool = cool_max after a switch, else max(tau_cool - 1, 0).
+ * The command is the chosen mode's first command (Algorithm 1's u*: zero if
+ * that mode failed validation).  The actuator post-processing of Algorithm 2
+ * (deadzone scaling) is hardware-specific and not part of the library. */
+#define EXACT_MAX_MODES 8
+typedef struct {
+    float lambda_switch;   /* switching penalty, >= 0 */
+    int cool_max;          /* tau_cool^max, >= 0: cycles after a switch that refuse another */
+} exact_hybrid_params;
+
+typedef struct exact_hybrid exact_hybrid;
+/* 1 <= n_modes <= EXACT_MAX_MODES; each mode obeys the exact_batch_create
+ * rules (its valid and nom_cost outputs may be NULL: the object then keeps
+ * its own).  Synchronous; allocates device memory; *out is released with
+ * exact_hybrid_destroy. */
+int exact_hybrid_create(int n_modes, const exact_scene *modes, const exact_hybrid_params *hp,
+                        exact_hybrid **out);
+void exact_hybrid_destroy(exact_hybrid *hybrid);
+/* One hybrid cycle on `stream` (no allocation, no host synchronisation:
+ * capturable in a CUDA graph).
+ *   mode_state device, 3 int32, in/out: [m_prev, tau_cool, stopped]; on
+ *              return [m*, tau_cool', 1 on a safe stop else 0]
+ *   u_out      device, 3: the chosen mode's first command, its n_u entries
+ *              followed by zeros (all zero on a safe stop)
+ *   Jbar       device, n_modes, or NULL: the augmented costs (+inf = invalid)
+ * Calls on one object must not overlap on the GPU. */
+int mppi_step_hybrid(exact_hybrid *hybrid, int *mode_state, float *u_out, float *Jbar, void *stream);
+/* The batch that runs the modes (for its tile autotuner). */
+exact_batch *exact_hybrid_batch(exact_hybrid *hybrid);
 
 #ifdef __cplusplus
 }

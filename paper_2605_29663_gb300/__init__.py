@@ -15,7 +15,7 @@ import threading
 
 from . import build as _build
 
-__all__ = ["load", "Footprint", "Context", "MppiParams", "sdf_batch", "mppi_step", "Batch", "ExactError", "MLP",
+__all__ = ["load", "Footprint", "Context", "MppiParams", "sdf_batch", "mppi_step", "Batch", "Hybrid", "ExactError", "MLP",
            "polar_hist", "proposal_features", "proposal_prepare", "proposal_select",
            "POLYGON", "RECTS", "DIFF", "ACKERMANN", "OMNI", "SPIN", "PARALLEL", "NU", "EXPORTS"]
 
@@ -31,7 +31,8 @@ EXPORTS = ["exact_status_string", "exact_footprint_create", "exact_footprint_des
            "mppi_step_noalloc", "exact_mlp_create", "exact_mlp_destroy", "exact_mlp_num_params",
            "exact_mlp_set_params", "exact_mlp_get_params", "exact_mlp_forward", "exact_mlp_loss_grad",
            "exact_mlp_train_step", "exact_polar_hist", "exact_proposal_features", "exact_proposal_prepare",
-           "exact_proposal_select"]
+           "exact_proposal_select", "exact_hybrid_create", "exact_hybrid_destroy", "mppi_step_hybrid",
+           "exact_hybrid_batch"]
 
 _lock = threading.Lock()
 _lib = None
@@ -113,6 +114,14 @@ def load() -> ctypes.CDLL:
         lib.exact_proposal_prepare.argtypes = [P, P, LL, P, P, P]
         lib.exact_proposal_select.restype = I
         lib.exact_proposal_select.argtypes = [P, P, I, I, P, P, P, P, I, I, P, P, P, P]
+        lib.exact_hybrid_create.restype = I
+        lib.exact_hybrid_create.argtypes = [I, P, P, ctypes.POINTER(P)]
+        lib.exact_hybrid_destroy.restype = V
+        lib.exact_hybrid_destroy.argtypes = [P]
+        lib.mppi_step_hybrid.restype = I
+        lib.mppi_step_hybrid.argtypes = [P, P, P, P, P]
+        lib.exact_hybrid_batch.restype = P
+        lib.exact_hybrid_batch.argtypes = [P]
         _lib = lib
         return lib
 
@@ -327,7 +336,56 @@ class ExactScene(ctypes.Structure):
                 ("U", ctypes.c_void_p), ("noise", ctypes.c_void_p), ("fp", ctypes.c_void_p),
                 ("params", MppiParams), ("u_star", ctypes.c_void_p), ("costs", ctypes.c_void_p),
                 ("weights", ctypes.c_void_p), ("valid", ctypes.c_void_p), ("U_upd", ctypes.c_void_p),
-                ("dmin", ctypes.c_void_p)]
+                ("dmin", ctypes.c_void_p), ("nom_cost", ctypes.c_void_p)]
+
+
+def _scene_array(scenes, dmin, costs, weights, U_upd, nom_cost):
+    """exact_scene array for a list of scene dicts (see Batch), the output
+    tensors allocated for each scene, and the tensors the array points into."""
+    torch = _torch()
+    keep = []
+    arr = (ExactScene * len(scenes))()
+    outputs = []
+    for i, sc in enumerate(scenes):
+        p = sc["params"] if isinstance(sc["params"], MppiParams) else MppiParams.from_dict(sc["params"])
+        K, T, nu = p.K, p.T, p.n_u
+        state = _dev(sc["state"], "state", torch.float32, (3,))
+        U = _dev(sc["U"], "U", torch.float32, (T, nu))
+        noise = _dev(sc["noise"], "noise", torch.float32, (K, T, nu))
+        wp = _dev(sc["waypoints"], "waypoints", torch.float32)
+        cloud = _dev(sc["cloud"], "cloud", torch.float32)
+        N = cloud.shape[0] if cloud.numel() else 0
+        mask = sc.get("mask")
+        if mask is not None:
+            mask = _dev(mask, "mask", torch.uint8, (N,))
+        dev = U.device
+        o = {"u_star": torch.empty(nu, dtype=torch.float32, device=dev),
+             "valid": torch.empty(1, dtype=torch.int32, device=dev)}
+        if costs:
+            o["costs"] = torch.empty(K, dtype=torch.float32, device=dev)
+        if weights:
+            o["weights"] = torch.empty(K, dtype=torch.float32, device=dev)
+        if U_upd:
+            o["U_upd"] = torch.empty((T, nu), dtype=torch.float32, device=dev)
+        if dmin:
+            o["dmin"] = torch.empty((K, T), dtype=torch.float32, device=dev)
+        if nom_cost:
+            o["nom_cost"] = torch.empty(1, dtype=torch.float32, device=dev)
+        outputs.append(o)
+        keep += [state, U, noise, wp, cloud, mask, sc["fp"]]
+        e = arr[i]
+        e.state, e.cloud, e.mask, e.n_points = state.data_ptr(), cloud.data_ptr() if N else None, \
+            None if mask is None else mask.data_ptr(), N
+        e.waypoints, e.n_wp, e.U, e.noise = wp.data_ptr(), wp.shape[0], U.data_ptr(), noise.data_ptr()
+        e.fp = sc["fp"].handle
+        e.params = p
+        e.u_star, e.valid = o["u_star"].data_ptr(), o["valid"].data_ptr()
+        e.costs = o["costs"].data_ptr() if costs else None
+        e.weights = o["weights"].data_ptr() if weights else None
+        e.U_upd = o["U_upd"].data_ptr() if U_upd else None
+        e.dmin = o["dmin"].data_ptr() if dmin else None
+        e.nom_cost = o["nom_cost"].data_ptr() if nom_cost else None
+    return arr, outputs, keep
 
 
 class Batch:
@@ -337,49 +395,11 @@ class Batch:
     `scenes` is a list of dicts with device tensors state, cloud, waypoints,
     U (in/out), noise, optional mask, a Footprint `fp` and `params`.  Output
     tensors (u_star, valid, costs, weights, U_upd, and dmin when
-    dmin=True) are allocated here and exposed as `outputs[i]`."""
+    dmin=True) are allocated here and exposed as `outputs[i]`; nom_cost=True
+    adds `nom_cost`, the cost J of each scene's updated nominal."""
 
-    def __init__(self, scenes, *, dmin=False, costs=True, weights=True, U_upd=True):
-        torch = _torch()
-        self._keep = []
-        arr = (ExactScene * len(scenes))()
-        self.outputs = []
-        for i, sc in enumerate(scenes):
-            p = sc["params"] if isinstance(sc["params"], MppiParams) else MppiParams.from_dict(sc["params"])
-            K, T, nu = p.K, p.T, p.n_u
-            state = _dev(sc["state"], "state", torch.float32, (3,))
-            U = _dev(sc["U"], "U", torch.float32, (T, nu))
-            noise = _dev(sc["noise"], "noise", torch.float32, (K, T, nu))
-            wp = _dev(sc["waypoints"], "waypoints", torch.float32)
-            cloud = _dev(sc["cloud"], "cloud", torch.float32)
-            N = cloud.shape[0] if cloud.numel() else 0
-            mask = sc.get("mask")
-            if mask is not None:
-                mask = _dev(mask, "mask", torch.uint8, (N,))
-            dev = U.device
-            o = {"u_star": torch.empty(nu, dtype=torch.float32, device=dev),
-                 "valid": torch.empty(1, dtype=torch.int32, device=dev)}
-            if costs:
-                o["costs"] = torch.empty(K, dtype=torch.float32, device=dev)
-            if weights:
-                o["weights"] = torch.empty(K, dtype=torch.float32, device=dev)
-            if U_upd:
-                o["U_upd"] = torch.empty((T, nu), dtype=torch.float32, device=dev)
-            if dmin:
-                o["dmin"] = torch.empty((K, T), dtype=torch.float32, device=dev)
-            self.outputs.append(o)
-            self._keep += [state, U, noise, wp, cloud, mask, sc["fp"]]
-            e = arr[i]
-            e.state, e.cloud, e.mask, e.n_points = state.data_ptr(), cloud.data_ptr() if N else None, \
-                None if mask is None else mask.data_ptr(), N
-            e.waypoints, e.n_wp, e.U, e.noise = wp.data_ptr(), wp.shape[0], U.data_ptr(), noise.data_ptr()
-            e.fp = sc["fp"].handle
-            e.params = p
-            e.u_star, e.valid = o["u_star"].data_ptr(), o["valid"].data_ptr()
-            e.costs = o["costs"].data_ptr() if costs else None
-            e.weights = o["weights"].data_ptr() if weights else None
-            e.U_upd = o["U_upd"].data_ptr() if U_upd else None
-            e.dmin = o["dmin"].data_ptr() if dmin else None
+    def __init__(self, scenes, *, dmin=False, costs=True, weights=True, U_upd=True, nom_cost=False):
+        arr, self.outputs, self._keep = _scene_array(scenes, dmin, costs, weights, U_upd, nom_cost)
         h = ctypes.c_void_p()
         _check(load().exact_batch_create(len(scenes), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(h)),
                "exact_batch_create")
@@ -407,6 +427,58 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             load().exact_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HybridParams(ctypes.Structure):
+    """Mirror of exact_hybrid_params."""
+    _fields_ = [("lambda_switch", ctypes.c_float), ("cool_max", ctypes.c_int)]
+
+
+class Hybrid:
+    """Hybrid-mode cycle (Algorithm 2, steps 1-2): the modes of one robot as
+    scenes (dicts as for Batch, each with its own motion model, U, noise and
+    params), advanced together, then the mode selection on the device.
+
+    `mode_state` (int32 [m_prev, tau_cool, stopped]) and `u` (float32 [3])
+    live on the device; `Jbar` holds the augmented costs of the last step and
+    `outputs[m]` each mode's Algorithm 1 outputs (with nom_cost)."""
+
+    def __init__(self, modes, lambda_switch: float, cool_max: int, *, m_prev: int = -1, costs=True,
+                 weights=False, U_upd=True):
+        torch = _torch()
+        arr, self.outputs, self._keep = _scene_array(modes, False, costs, weights, U_upd, True)
+        dev = self.outputs[0]["u_star"].device
+        hp = HybridParams(float(lambda_switch), int(cool_max))
+        h = ctypes.c_void_p()
+        _check(load().exact_hybrid_create(len(modes), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(hp),
+                                          ctypes.byref(h)), "exact_hybrid_create")
+        self._h = h
+        self.n = len(modes)
+        self.mode_state = torch.tensor([int(m_prev), 0, 0], dtype=torch.int32, device=dev)
+        self.u = torch.zeros(3, dtype=torch.float32, device=dev)
+        self.Jbar = torch.empty(self.n, dtype=torch.float32, device=dev)
+
+    def step(self, stream=None):
+        _check(load().mppi_step_hybrid(self._h, self.mode_state.data_ptr(), self.u.data_ptr(),
+                                       self.Jbar.data_ptr(), _stream(stream)), "mppi_step_hybrid")
+
+    def autotune(self, iters: int = 3, stream=None) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(8192)
+        b = load().exact_hybrid_batch(self._h)
+        _check(load().exact_batch_autotune(b, iters, buf, 8192, _stream(stream)), "exact_batch_autotune")
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().exact_hybrid_destroy(self._h)
             self._h = None
 
     def __del__(self):

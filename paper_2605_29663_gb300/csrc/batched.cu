@@ -202,7 +202,7 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         V.U = S.U;
         V.noise = S.noise;
         V.u_star = S.u_star; V.costs = S.costs; V.weights = S.weights; V.U_upd_out = S.U_upd;
-        V.dmin = S.dmin; V.valid = S.valid;
+        V.dmin = S.dmin; V.valid = S.valid; V.nom_cost = S.nom_cost;
         V.hdr = reinterpret_cast<ArenaHeader *>(b->d_ctrl + kHdrStride * s);
         carve_scene(V, scratch + scratch_off[s], S.params.K, S.params.T, 1);
         V.upd_chunk = upd_chunk_for(S.params.K, S.params.T, S.params.n_u);
@@ -229,7 +229,8 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_upd, upd.data(), upd.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_val, val.data(), val.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(b->d_ctrl, 0, ctrl_bytes) != cudaSuccess)
+        cudaMemset(b->d_ctrl, 0, ctrl_bytes) != cudaSuccess ||
+        (scratch_total && cudaMemset(scratch, 0, scratch_total) != cudaSuccess))
         rc = EXACT_ECUDA;
     if (rc == EXACT_OK) rc = batch_grid(b);
     if (rc != EXACT_OK) {

@@ -37,6 +37,7 @@ struct SceneView {
     float *U;
     const float *noise;
     float *u_star, *costs, *weights, *U_upd_out, *dmin;
+    float *nom_cost;    // 1 or NULL: cost J of the updated nominal
     int *valid;
     ArenaHeader *hdr;   // beta, tickets, validation flag
     double *Jt;         // K   J~ = J + w_inf I(chi)
@@ -44,6 +45,7 @@ struct SceneView {
     float *part;        // G x (T*nu + 1) partial sums
     unsigned *dkey;     // K x T  per-step keys exchanged between horizon parts
     unsigned *tk;       // K      finished horizon parts of each sample
+    unsigned *vkey;     // T      nominal's per-step minimum key (complemented order key; 0 = empty)
     int upd_chunk, upd_blocks, val_chunks;
     int parts;          // blocks per sample (horizon split); 1 = one block per sample
 };
@@ -91,6 +93,7 @@ inline size_t scene_scratch_bytes(int K, int T, int parts) {
     b += align_up((size_t)K * sizeof(double), 256);
     b += align_up((size_t)K * sizeof(float), 256);
     b += align_up((size_t)upd_blocks_for(K, T, 3) * (T * 3 + 1) * sizeof(float), 256);
+    b += align_up((size_t)T * sizeof(unsigned), 256);
     if (parts > 1) {
         b += align_up((size_t)K * T * sizeof(unsigned), 256);
         b += align_up((size_t)K * sizeof(unsigned), 256);
@@ -101,6 +104,7 @@ inline void carve_scene(SceneView &V, char *p, int K, int T, int parts) {
     V.Jt = reinterpret_cast<double *>(p); p += align_up((size_t)K * sizeof(double), 256);
     V.wt = reinterpret_cast<float *>(p); p += align_up((size_t)K * sizeof(float), 256);
     V.part = reinterpret_cast<float *>(p); p += align_up((size_t)upd_blocks_for(K, T, 3) * (T * 3 + 1) * sizeof(float), 256);
+    V.vkey = reinterpret_cast<unsigned *>(p); p += align_up((size_t)T * sizeof(unsigned), 256);
     V.parts = parts;
     V.dkey = nullptr;
     V.tk = nullptr;
@@ -439,7 +443,11 @@ struct ValidateSmem {
 // over its chunk of points.  Block 0 also writes U_upd and the blocks share
 // out the normalised weights and the costs.  The scene's last block (atomic
 // ticket) writes u*, the shifted (last entry repeated) or reset U, the valid
-// flag, and empties beta for the next cycle.
+// flag, and empties beta for the next cycle.  When the nominal's cost is
+// requested, every block also publishes the minimum key of its chunk of its
+// step (one complemented 32-bit order key per step, atomicMax) and the last
+// block scores the nominal exactly like a sample (Sec. III-E, IV-E; the cost
+// J_m of Algorithm 2) and empties the step keys.
 template <class EV>
 __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, int h, int c, ValidateSmem &sm) {
     const MppiP &P = V.P;
@@ -519,6 +527,7 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
         for (int w = 1; w < kBlock / 32; ++w) b = fminf(b, sm.mn[w]);
         const float d = b == finf() ? finf() : ev.dist(b);
         if (!(d >= P.d_safe)) atomicExch(&V.hdr->bad, 1);
+        if (V.nom_cost) atomicMax(V.vkey + h, ~f2ord(b));
         __threadfence();
         sm.last = atomicAdd(&V.hdr->ticket[1], 1u) == (unsigned)nblocks - 1;
     }
@@ -534,6 +543,26 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
     if (tid == 0) {
         if (V.valid) *V.valid = ok;
         V.hdr->beta_enc = 0ull;
+    }
+    if (V.nom_cost && warp == 0) {
+        LaneRollout R;
+        warp_rollout(P, V.state[0], V.state[1], V.state[2], [&](int hh, int j) { return clamp_u(P, j, sm.U[hh * nu + j]); },
+                     R);
+        double acc = 0.0;
+#pragma unroll
+        for (int e = 0; e < kMaxPerLane; ++e) {
+            const int hh = lane * R.per + e;
+            if (e < R.per && hh < T) {
+                const float u2 = fmaf(R.u[e][0], R.u[e][0], fmaf(R.u[e][1], R.u[e][1], R.u[e][2] * R.u[e][2]));
+                const float stage = fmaf(P.w_goal, guidance_dist(R.x[e], R.y[e], V.wp, V.W), P.w_ctrl * u2);
+                const float key = ord2f(~atomicExch(V.vkey + hh, 0u));
+                const float d = key == finf() ? finf() : ev.dist(key);
+                acc += (double)stage + phi_obs_d(P, d);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) *V.nom_cost = (float)(acc + (double)(P.w_term * guidance_dist(R.qTx, R.qTy, V.wp, V.W)));
     }
 }
 

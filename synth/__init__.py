@@ -208,3 +208,43 @@ def batched(seed=0, n_scenes=64, scale=1.0) -> list:
         T = int(g.integers(20, 51))
         scenes.append(random_scene(g, model, E, max(N, 8), max(K, 4), T))
     return scenes
+
+
+def ranger_footprint() -> np.ndarray:
+    """Hybrid-platform footprint (reading): a 0.74 x 0.50 m chassis with a
+    0.30 x 0.20 m payload overhanging the front-left corner, CCW."""
+    return np.array([[-0.37, -0.25], [0.37, -0.25], [0.37, 0.25], [0.25, 0.25], [0.25, 0.45],
+                     [-0.05, 0.45], [-0.05, 0.25], [-0.37, 0.25]], dtype=np.float32)
+
+
+def hybrid(seed=0, K=1024, T=20, N=2048) -> list:
+    """Hybrid-mode workload: one robot with three motion modes (Ackermann,
+    parallel, spin) in a corridor with a side pocket and boxes; the goal lies
+    beside the robot so that lateral motion is the short way.  Returns one
+    scene dict per mode; they share state, cloud, mask, waypoints, footprint.
+    Mode limits follow the platform table of the paper (|v| <= 1.5 m/s,
+    |v_para| <= 0.6 m/s, |omega| <= 1 rad/s); the steering limit and the
+    noise scales are readings."""
+    g = rng(seed)
+    xs = np.arange(-4.0, 4.0, 0.02)
+    walls = [np.stack([xs, np.full_like(xs, -0.9)], 1), np.stack([xs[np.abs(xs) > 0.8], np.full_like(xs[np.abs(xs) > 0.8], 0.9)], 1)]
+    ys = np.arange(0.9, 3.2, 0.02)
+    walls += [np.stack([np.full_like(ys, -0.8), ys], 1), np.stack([np.full_like(ys, 0.8), ys], 1)]
+    for _ in range(12):
+        cx, cy = g.uniform(-4.0, 4.0), g.choice([-1.0, 1.0]) * g.uniform(1.6, 4.0)
+        walls.append(box_edge_points(cx, cy, g.uniform(0.2, 0.6), g.uniform(0.2, 0.6), 0.02))
+    pts = np.concatenate(walls)
+    pts = pts + g.normal(0.0, 0.01, size=pts.shape)
+    cloud, mask = fit_budget(g, pts, N)
+    common = dict(q0=np.zeros(3, dtype=np.float32), cloud=cloud, mask=mask,
+                  waypoints=np.array([[0.0, 2.6]], dtype=np.float32), kind=POLYGON, fp=ranger_footprint())
+    modes = []
+    for model, sigma, lo, hi in ((ACKERMANN, (0.4, 0.3), (-1.5, -0.6), (1.5, 0.6)),
+                                 (PARALLEL, (0.3,), (-0.6,), (0.6,)),
+                                 (SPIN, (0.5,), (-1.0,), (1.0,))):
+        nu = NU[model]
+        u_min = list(lo) + [-1e30] * (3 - nu)
+        u_max = list(hi) + [1e30] * (3 - nu)
+        p = mppi_params(K, T, model, wheelbase=0.5, clamp=1, u_min=u_min, u_max=u_max)
+        modes.append(dict(common, U=np.zeros((T, nu), dtype=np.float32), eps=noise(g, K, T, sigma), params=p))
+    return modes
