@@ -65,7 +65,7 @@ def lib():
             _lib.ox_sdf_batch.argtypes = [P, P, I, P, I, I, P, I, P, P, P]
             _lib.ox_rollout.argtypes = [I, D, P, P, I, I, D, P]
             _lib.ox_mppi_step.restype = I
-            _lib.ox_mppi_step.argtypes = [P, P, P, P, I, P, I, P, P, I, P, I,
+            _lib.ox_mppi_step.argtypes = [P, P, P, P, P, I, P, I, P, P, I, P, I,
                                           P, P, P, P, P, P, P, P, P, D]
             _lib.ox_hybrid_select.restype = I
             _lib.ox_hybrid_select.argtypes = [I, P, P, D, I, P, P, P]
@@ -184,16 +184,18 @@ def make_params(d: dict) -> Params:
 
 
 def mppi_step(params: dict, q0, cloud, waypoints, U, eps, kind: int, fp, mask=None,
-              near_tol: float = 1e-5) -> dict:
+              near_tol: float = 1e-5, vel=None) -> dict:
     """One control cycle of Algorithm 1.  Returns a dict with U (shifted or reset),
     U_upd (updated nominal), u_star, costs (J~), weights (omega), valid,
     dmin (K x T), dmin_nom (T), J_nom (cost of the updated nominal) and n_near
-    (threshold-adjacent d_min count)."""
+    (threshold-adjacent d_min count).  vel (N x 2): point velocities, each
+    step scored against the predicted points o + t_h v."""
     P = make_params(params)
     K, T, nu = P.K, P.T, P.nu
     pts = _f64(cloud, (-1, 2))
     N = pts.shape[0]
     m = _mask(mask, N)
+    v = None if vel is None else _f64(vel, (N, 2))
     wp = _f64(waypoints, (-1, 2))
     Uio = _f64(U, (T, nu)).copy()
     e = _f64(eps, (K, T, nu))
@@ -209,6 +211,7 @@ def mppi_step(params: dict, q0, cloud, waypoints, U, eps, kind: int, fp, mask=No
     J_nom = ctypes.c_double(0.0)
     n_near = ctypes.c_int(0)
     rc = lib().ox_mppi_step(ctypes.byref(P), q.ctypes.data, pts.ctypes.data,
+                            None if v is None else v.ctypes.data,
                             None if m is None else m.ctypes.data, N,
                             wp.ctypes.data, wp.shape[0], Uio.ctypes.data, e.ctypes.data,
                             kind, f.ctypes.data, f.shape[0],
@@ -244,7 +247,7 @@ def hybrid_step(modes, hp: dict, m_prev: int, tau: int, near_tol: float = 1e-5) 
     outs = []
     for md in modes:
         o = mppi_step(md["params"], md["q0"], md["cloud"], md["waypoints"], md["U"], md["eps"], md["kind"],
-                      md["fp"], mask=md.get("mask"), near_tol=near_tol)
+                      md["fp"], mask=md.get("mask"), near_tol=near_tol, vel=md.get("vel"))
         md["U"] = o["U"]
         outs.append(o)
     J = [o["J_nom"] for o in outs]

@@ -270,9 +270,13 @@ static int near_threshold(double d, double d_safe, double tol) {
 
 /* Cost of one control sequence u (T x nu, already clamped), Sec. III-E cost
  * J plus the unsafe flag chi (Sec. IV-E).  dmin_out (T) may be NULL; *near
- * counts horizon steps whose d_min lies within tol of 0 or d_safe. */
+ * counts horizon steps whose d_min lies within tol of 0 or d_safe.
+ * vel (N x 2) or NULL: time-indexed obstacle prediction (the extension of
+ * Sec. VI) -- at step h the points are at o + t v, t = (h + state_offset) dt
+ * the time of the scored state; moved (N x 2) is scratch for them. */
 static double sequence_cost(const ox_params *P, const double q0[3], const double *u,
-                            const double *cloud, const uint8_t *mask, int N,
+                            const double *cloud, const double *vel, double *moved,
+                            const uint8_t *mask, int N,
                             const double *wp, int W, int kind, const double *fp, int n,
                             double *states, double *dmin_out, int *chi_out,
                             int *near, double tol) {
@@ -282,7 +286,13 @@ static double sequence_cost(const ox_params *P, const double q0[3], const double
     int chi = 0, nn = 0;
     for (int h = 0; h < T; ++h) {
         const double *s = states + 3 * (h + P->state_offset);
-        double d = ox_dmin_pose(cloud, mask, N, s[0], s[1], s[2], kind, fp, n, NULL);
+        const double *pts = cloud;
+        if (vel) {
+            double t = (double)(h + P->state_offset) * P->dt;
+            for (int i = 0; i < 2 * N; ++i) moved[i] = cloud[i] + t * vel[i];
+            pts = moved;
+        }
+        double d = ox_dmin_pose(pts, mask, N, s[0], s[1], s[2], kind, fp, n, NULL);
         if (dmin_out) dmin_out[h] = d;
         double u2 = 0.0;
         for (int j = 0; j < nu; ++j) u2 += u[h * nu + j] * u[h * nu + j];
@@ -307,8 +317,9 @@ static double clamp_dim(const ox_params *P, int j, double u) {
 }
 
 /* Algorithm 1, one batched control cycle, followed step by step.
- *   in : q0 (3), cloud (N x 2) + mask (N or NULL), waypoints (W x 2),
- *        U (T x nu), eps (K x T x nu), footprint.
+ *   in : q0 (3), cloud (N x 2) + mask (N or NULL), vel (N x 2 point
+ *        velocities for time-indexed predictions, or NULL), waypoints
+ *        (W x 2), U (T x nu), eps (K x T x nu), footprint.
  *   out: U (T x nu, shifted or reset), u_star (nu), costs J~ (K), weights
  *        omega (K), *valid, U_upd (updated nominal before shift/reset),
  *        dmin (K x T) and dmin_nom (T) when non-NULL, *J_nom = the cost J of
@@ -318,7 +329,7 @@ static double clamp_dim(const ox_params *P, int j, double u) {
  *        disagree).
  * Returns 0, or -1 on bad arguments / allocation failure. */
 int ox_mppi_step(const ox_params *P, const double q0[3],
-                 const double *cloud, const uint8_t *mask, int N,
+                 const double *cloud, const double *vel, const uint8_t *mask, int N,
                  const double *wp, int W, double *U, const double *eps,
                  int kind, const double *fp, int n,
                  double *u_star, double *costs, double *weights, int *valid,
@@ -336,6 +347,7 @@ int ox_mppi_step(const ox_params *P, const double q0[3],
     for (int r = 0; r < K; ++r) {
         double *u = (double *)malloc(sizeof(double) * (size_t)T * nu);
         double *st = (double *)malloc(sizeof(double) * (size_t)(T + 1) * 3);
+        double *mv = vel ? (double *)malloc(sizeof(double) * (size_t)2 * (N > 0 ? N : 1)) : NULL;
         for (int h = 0; h < T; ++h)
             for (int j = 0; j < nu; ++j) {
                 int64_t k = ((int64_t)r * T + h) * nu + j;
@@ -346,12 +358,12 @@ int ox_mppi_step(const ox_params *P, const double q0[3],
                 epsc[k] = P->clamp ? v - uh : eps[k];
             }
         int chi = 0, nn = 0;
-        double J = sequence_cost(P, q0, u, cloud, mask, N, wp, W, kind, fp, n, st,
+        double J = sequence_cost(P, q0, u, cloud, vel, mv, mask, N, wp, W, kind, fp, n, st,
                                  dmin ? dmin + (int64_t)r * T : NULL, &chi, &nn, near_tol);
         /* Step 3: J~ = J + w_inf I(chi). */
         Jt[r] = J + P->w_inf * (chi ? 1.0 : 0.0);
         near_total += nn;
-        free(u); free(st);
+        free(u); free(st); free(mv);
     }
 
     /* Step 3: beta = min J~, omega = exp(-(J~ - beta)/lambda) / sum. */
@@ -377,10 +389,12 @@ int ox_mppi_step(const ox_params *P, const double q0[3],
     double *u = (double *)malloc(sizeof(double) * (size_t)T * nu);
     double *st = (double *)malloc(sizeof(double) * (size_t)(T + 1) * 3);
     double *dn = (double *)malloc(sizeof(double) * (size_t)T);
+    double *mv = vel ? (double *)malloc(sizeof(double) * (size_t)2 * (N > 0 ? N : 1)) : NULL;
     for (int h = 0; h < T; ++h)
         for (int j = 0; j < nu; ++j) u[h * nu + j] = clamp_dim(P, j, U[h * nu + j]);
     int chi_nom = 0, nn = 0;
-    double Jn = sequence_cost(P, q0, u, cloud, mask, N, wp, W, kind, fp, n, st, dn, &chi_nom, &nn, near_tol);
+    double Jn = sequence_cost(P, q0, u, cloud, vel, mv, mask, N, wp, W, kind, fp, n, st, dn, &chi_nom, &nn,
+                              near_tol);
     if (J_nom) *J_nom = Jn;
     int ok = 1;
     for (int h = 0; h < T; ++h) if (!(dn[h] >= P->d_safe)) ok = 0;
@@ -399,7 +413,7 @@ int ox_mppi_step(const ox_params *P, const double q0[3],
     }
     if (valid) *valid = ok;
     if (n_near) *n_near = near_total;
-    free(u); free(st); free(dn); free(epsc); free(Jt);
+    free(u); free(st); free(dn); free(mv); free(epsc); free(Jt);
     return 0;
 }
 

@@ -66,6 +66,23 @@ def forklift_rects() -> np.ndarray:
                     dtype=np.float32)
 
 
+def rectilinear_shapes() -> dict:
+    """The L-, T- and F-shaped rectilinear bodies of the rectangle-cover vs
+    polygon comparison (Experiment 1; the paper gives no dimensions, so these
+    are readings).  name -> (polygon outline (CCW), rectangle cover (cx, cy,
+    sx, sy) of the same set; covering boxes overlap, never just touch), in float64."""
+    L_poly = np.array([(-0.5, -0.3), (0.5, -0.3), (0.5, 1.1), (0.2, 1.1), (0.2, 0.3), (-0.5, 0.3)])
+    L_rects = np.array([(0.0, 0.0, 0.5, 0.3), (0.35, 0.55, 0.15, 0.55)], dtype=np.float64)
+    T_poly = np.array([(-0.15, -0.6), (0.15, -0.6), (0.15, 0.3), (0.6, 0.3), (0.6, 0.6), (-0.6, 0.6),
+                       (-0.6, 0.3), (-0.15, 0.3)], dtype=np.float64)
+    T_rects = np.array([(0.0, 0.45, 0.6, 0.15), (0.0, -0.075, 0.15, 0.525)], dtype=np.float64)
+    F_poly = np.array([(-0.5, -0.6), (-0.2, -0.6), (-0.2, -0.1), (0.2, -0.1), (0.2, 0.15), (-0.2, 0.15),
+                       (-0.2, 0.35), (0.4, 0.35), (0.4, 0.6), (-0.5, 0.6)], dtype=np.float64)
+    F_rects = np.array([(-0.35, 0.0, 0.15, 0.6), (-0.05, 0.475, 0.45, 0.125), (-0.15, 0.025, 0.35, 0.125)],
+                       dtype=np.float64)
+    return {"L": (L_poly, L_rects), "T": (T_poly, T_rects), "F": (F_poly, F_rects)}
+
+
 # ----------------------------------------------------------------- obstacles
 def uniform_points(g, n, lo, hi) -> np.ndarray:
     return g.uniform(lo, hi, size=(n, 2)).astype(np.float32)
@@ -248,3 +265,38 @@ def hybrid(seed=0, K=1024, T=20, N=2048) -> list:
         p = mppi_params(K, T, model, wheelbase=0.5, clamp=1, u_min=u_min, u_max=u_max)
         modes.append(dict(common, U=np.zeros((T, nu), dtype=np.float32), eps=noise(g, K, T, sigma), params=p))
     return modes
+
+
+def dynamic_scene(seed=0, K=1024, T=20, N=2048, n_discs=40, speed=0.5) -> dict:
+    """Moving-obstacle workload for time-indexed predictions: diff-drive
+    robot with the L footprint, goal 6 m ahead, 8 static boxes and n_discs
+    discs of radius 0.3 m moving at `speed` m/s in random directions within
+    10 m, all sampled every 0.05 m; `vel` gives every point its obstacle's
+    velocity (zero for the boxes).  Fitted to N points (subsample, or zero
+    padding plus mask; padded points get zero velocity)."""
+    g = rng(seed)
+    pts, vel = [], []
+    for _ in range(8):
+        c = (g.uniform(1.5, 6.0), g.uniform(-2.5, 2.5))
+        b = box_edge_points(c[0], c[1], g.uniform(0.3, 1.0), g.uniform(0.3, 1.0), 0.05)
+        pts.append(b)
+        vel.append(np.zeros_like(b))
+    for _ in range(n_discs):
+        r, a = g.uniform(1.5, 10.0), g.uniform(-math.pi, math.pi)
+        d = disc_edge_points(r * math.cos(a), r * math.sin(a), 0.3, 0.05)
+        h = g.uniform(-math.pi, math.pi)
+        pts.append(d)
+        vel.append(np.tile([speed * math.cos(h), speed * math.sin(h)], (d.shape[0], 1)))
+    allp, allv = np.concatenate(pts), np.concatenate(vel)
+    M = allp.shape[0]
+    if M >= N:
+        idx = np.sort(g.choice(M, N, replace=False))
+        cloud, v, mask = allp[idx], allv[idx], None
+    else:
+        cloud = np.zeros((N, 2)); v = np.zeros((N, 2))
+        cloud[:M], v[:M] = allp, allv
+        mask = np.zeros(N, np.uint8); mask[:M] = 1
+    return dict(q0=np.zeros(3, dtype=np.float32), cloud=cloud.astype(np.float32), vel=v.astype(np.float32),
+                mask=mask, waypoints=np.array([[6.0, 0.0]], dtype=np.float32),
+                U=np.zeros((T, 2), dtype=np.float32), eps=noise(g, K, T, (0.3, 0.6)),
+                kind=POLYGON, fp=l_footprint(), params=mppi_params(K, T, DIFF))
