@@ -244,6 +244,47 @@ def mppi_extra(torch, ex, dev, cpu: bool = True):
     return out
 
 
+def predicted_extra(torch, ex, dev, cpu: bool = True):
+    """Time-indexed obstacle predictions: the dynamic scene (diff-drive, L
+    footprint, K = 1024, T = 20, N = 2048: 8 boxes and 40 discs at 0.5 m/s)
+    through mppi_step_predicted, and the same scene as a static cloud through
+    mppi_step, both replayed from CUDA graphs."""
+    import synth
+    s = synth.dynamic_scene(0)
+    p = s["params"]
+    fp = ex.Footprint(s["kind"], s["fp"])
+    t = {k: torch.from_numpy(s[k]).to(dev) for k in ("q0", "cloud", "vel", "waypoints", "U", "eps")}
+    mask = torch.from_numpy(s["mask"]).to(dev) if s["mask"] is not None else None
+    ctx = ex.Context()
+    ctx.reserve(0, p["K"], p["T"])
+    out = {}
+    res = {}
+    for name, vel in (("predicted", t["vel"]), ("static", None)):
+        U = t["U"].clone()
+
+        def step():
+            out.update(ex.mppi_step(ctx, t["q0"], t["cloud"], t["waypoints"], U, t["eps"], fp, p, mask=mask,
+                                    velocity=vel, out=out))
+        step()
+        res[name + "_us_per_step"] = 1e3 * time_graph(torch, step, 1000)
+    N = s["cloud"].shape[0]
+    evals = p["K"] * p["T"] * N * s["fp"].shape[0]
+    res.update({"K": p["K"], "T": p["T"], "N": N, "footprint": f"polygonx{s['fp'].shape[0]}",
+                "evals_per_step": evals,
+                "predicted_counted_tflops": FLOPS_PER_POINT_EDGE * evals / (res["predicted_us_per_step"] * 1e-6) / 1e12,
+                "overhead_vs_static": res["predicted_us_per_step"] / res["static_us_per_step"],
+                "timing": "CUDA graph replay, events, inputs L2-resident"})
+    if cpu:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.mppi_step(p, s["q0"], s["cloud"], s["waypoints"], s["U"], s["eps"], s["kind"], s["fp"],
+                         mask=s["mask"], vel=s["vel"])
+        res["cpu_oracle"] = {"ms_per_step": 1e3 * (time.perf_counter() - t0), "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": "1 full predicted cycle, float64, OpenMP over samples"}
+    return res
+
+
 def hybrid_extra(torch, ex, dev, cpu: bool = True):
     """Hybrid-mode cycle (three modes of one robot: Ackermann, parallel, spin;
     K = 1024 each, T = 20, N = 2048, 8-vertex footprint): the batched launch set
@@ -277,6 +318,112 @@ def hybrid_extra(torch, ex, dev, cpu: bool = True):
         out["cpu_oracle"] = {"ms_per_cycle": 1e3 * dt, "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": "1 full hybrid cycle (3 modes), float64, OpenMP over samples"}
     return out
+
+
+def _per_call(torch, fn, trials: int = 100, warm: int = 5, pre=None):
+    """Per-call times in microseconds: the device time of the call replayed
+    from CUDA graphs (each graph holds 20 calls; mean and spread over `trials`
+    / 20 replays), so that the host's launch cost is not counted, and the host
+    wall time of a plain call through the Python binding with a synchronize
+    after each.  `pre` (e.g. an L2 flush) runs before every timed call,
+    outside the timed region; with `pre` the device time comes from events
+    around each plain call instead of graphs."""
+    import statistics
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    if pre is None:
+        per_graph = 20
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fn()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            for _ in range(per_graph):
+                fn()
+        gr.replay()
+        torch.cuda.synchronize()
+        reps = max(3, trials // per_graph)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in ev:
+            e0.record()
+            gr.replay()
+            e1.record()
+        torch.cuda.synchronize()
+        dev_us = [1e3 * e0.elapsed_time(e1) / per_graph for e0, e1 in ev]
+    else:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(trials)]
+        for e0, e1 in ev:
+            pre()
+            e0.record()
+            fn()
+            e1.record()
+        torch.cuda.synchronize()
+        dev_us = [1e3 * e0.elapsed_time(e1) for e0, e1 in ev]
+    wall = []
+    for _ in range(trials):
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        wall.append(1e6 * (time.perf_counter() - t0))
+    return {"device_us_mean": statistics.mean(dev_us), "device_us_std": statistics.pstdev(dev_us),
+            "wall_us_mean": statistics.mean(wall), "wall_us_std": statistics.pstdev(wall), "trials": trials}
+
+
+def sdf_extra(torch, ex, dev):
+    """Experiment 1 counterparts: (a) rectangle cover vs polygon edges on the
+    L-, T- and F-shaped bodies -- one pose x 100,000 points uniform in a
+    50 x 50 m square per call (the paper's per-call setting), and 4,096 poses x
+    8,192 points (full matrix) where the arithmetic dominates; (b) per-call time
+    against the number of query points, 1e2 .. 1e6, one pose."""
+    import numpy as np
+
+    import synth
+    g = synth.rng(7)
+    ctx = ex.Context()
+    pts100k = torch.from_numpy(synth.uniform_points(g, 100_000, -25.0, 25.0)).to(dev)
+    pose1 = torch.zeros((1, 3), dtype=torch.float32, device=dev)
+    P, N = 4096, 8192
+    poses = torch.from_numpy(synth.sdf_microbench(seed=7, n_poses=P, n_points=8, n_vertices=4)["poses"]).to(dev)
+    pts8k = torch.from_numpy(synth.uniform_points(g, N, -6.0, 6.0)).to(dev)
+    d100k = {"dist": torch.empty((1, 100_000), device=dev), "dmin": torch.empty(1, device=dev),
+             "argmin": torch.empty(1, dtype=torch.int32, device=dev)}
+    dbig = {"dist": torch.empty((P, N), device=dev), "dmin": torch.empty(P, device=dev),
+            "argmin": torch.empty(P, dtype=torch.int32, device=dev)}
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    shapes = {}
+    for name, (poly, rects) in synth.rectilinear_shapes().items():
+        row = {"edges": int(poly.shape[0]), "boxes": int(rects.shape[0])}
+        for kind, fpd in (("rect", (synth.RECTS, rects)), ("poly", (synth.POLYGON, poly))):
+            fp = ex.Footprint(fpd[0], fpd[1].astype(np.float32))
+            row[kind + "_per_call_100k"] = _per_call(
+                torch, lambda: ex.sdf_batch(pts100k, pose1, fp, ctx=ctx, out=d100k))
+
+            t = _per_call(torch, lambda: ex.sdf_batch(pts8k, poses, fp, ctx=ctx, out=dbig), trials=20,
+                          pre=flush.zero_)
+            row[kind + "_full_matrix_us"] = t["device_us_mean"]
+        row["speedup_per_call_100k"] = row["poly_per_call_100k"]["device_us_mean"] / \
+            row["rect_per_call_100k"]["device_us_mean"]
+        row["speedup_full_matrix"] = row["poly_full_matrix_us"] / row["rect_full_matrix_us"]
+        shapes[name] = row
+    scaling = {}
+    l_poly, l_rects = synth.rectilinear_shapes()["L"]
+    fps = {"L_polygon": ex.Footprint(synth.POLYGON, l_poly.astype(np.float32)),
+           "L_rects": ex.Footprint(synth.RECTS, l_rects.astype(np.float32)),
+           "star32": ex.Footprint(synth.POLYGON, synth.star_polygon(synth.rng(3), 32, 0.3, 1.2))}
+    for n in (100, 1_000, 10_000, 100_000, 1_000_000):
+        pts = torch.from_numpy(synth.uniform_points(g, n, -25.0, 25.0)).to(dev)
+        o = {"dist": torch.empty((1, n), device=dev), "dmin": torch.empty(1, device=dev),
+             "argmin": torch.empty(1, dtype=torch.int32, device=dev)}
+        scaling[str(n)] = {k: _per_call(torch, lambda: ex.sdf_batch(pts, pose1, f, ctx=ctx, out=o))
+                           for k, f in fps.items()}
+    return {"rect_vs_poly": shapes, "sdf_scaling": scaling,
+            "setup": "per call: one exact_sdf_batch with distances + min + argmin; device time per call from CUDA "
+                     "graphs of 20 calls, wall time of a plain call through the Python binding with a synchronize; "
+                     "full matrix: 4096 poses x 8192 points, L2 flushed before each call outside the events"}
 
 
 def oracle_mppi_sample(s, budget_s: float = 3.0) -> dict:
@@ -513,6 +660,8 @@ def run_gpu(args):
         line["extra"] = mppi_extra(torch, ex, dev, cpu=not args.no_cpu)
         line["extra"]["batched64"] = batched_extra(torch, ex, dev)
         line["extra"]["hybrid3"] = hybrid_extra(torch, ex, dev, cpu=not args.no_cpu)
+        line["extra"]["predicted"] = predicted_extra(torch, ex, dev, cpu=not args.no_cpu)
+        line["extra"].update(sdf_extra(torch, ex, dev))
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

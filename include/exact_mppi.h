@@ -153,6 +153,22 @@ int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint
               float *u_star, float *costs, float *weights, int *valid, float *U_upd,
               float *dmin, void *stream);
 
+/* mppi_step with time-indexed obstacle predictions (the extension named in
+ * Sec. VI: signed-distance costs against predicted obstacle positions along
+ * the horizon instead of the current observation only).  Every point i has a
+ * velocity v_i and at horizon step h it is evaluated at the constant-velocity
+ * prediction o_i + t_h v_i, t_h = (h + state_offset) dt being the time of the
+ * scored state (the validation of the updated nominal uses the same
+ * predictions).  velocity: device, n_points x 2 (m/s), 8-byte aligned,
+ * required when n_points > 0; a point whose predicted position is not finite
+ * is ignored like a masked one.  Everything else as mppi_step; zero
+ * velocities give mppi_step's results. */
+int mppi_step_predicted(exact_ctx *ctx, const float *state, const float *cloud, const float *velocity,
+                        const uint8_t *mask, int n_points, const float *waypoints, int n_wp, float *U,
+                        const float *noise, const exact_footprint *fp, const exact_mppi_params *params,
+                        float *u_star, float *costs, float *weights, int *valid, float *U_upd,
+                        float *dmin, void *stream);
+
 /* ------------------------------------------------------------------ learned proposal
  * Project extension (the paper has no learned component): a small network
  * shifts the sampling mean of MPPI; plain MPPI on the same noise remains the

@@ -26,7 +26,8 @@ NU = {DIFF: 2, ACKERMANN: 2, OMNI: 3, SPIN: 1, PARALLEL: 1}
 # every symbol declared in include/exact_mppi.h
 EXPORTS = ["exact_status_string", "exact_footprint_create", "exact_footprint_destroy",
            "exact_footprint_info", "exact_ctx_create", "exact_ctx_destroy", "exact_ctx_reserve",
-           "exact_ctx_get_error", "exact_sdf_batch", "mppi_step", "exact_batch_create", "exact_batch_destroy",
+           "exact_ctx_get_error", "exact_sdf_batch", "mppi_step", "mppi_step_predicted", "exact_batch_create",
+           "exact_batch_destroy",
            "mppi_step_batched", "exact_batch_autotune", "exact_batch_get_tiles", "exact_batch_set_tiles",
            "mppi_step_noalloc", "exact_mlp_create", "exact_mlp_destroy", "exact_mlp_num_params",
            "exact_mlp_set_params", "exact_mlp_get_params", "exact_mlp_forward", "exact_mlp_loss_grad",
@@ -75,6 +76,8 @@ def load() -> ctypes.CDLL:
         lib.exact_sdf_batch.argtypes = [P, P, P, I, P, I, P, P, P, P, P]
         lib.mppi_step.restype = I
         lib.mppi_step.argtypes = [P, P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
+        lib.mppi_step_predicted.restype = I
+        lib.mppi_step_predicted.argtypes = [P, P, P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
         lib.exact_batch_create.restype = I
         lib.exact_batch_create.argtypes = [I, P, ctypes.POINTER(P)]
         lib.exact_batch_destroy.restype = V
@@ -291,11 +294,12 @@ class MppiParams(ctypes.Structure):
 
 
 def mppi_step(ctx: Context, state, cloud, waypoints, U, noise, footprint: Footprint, params, mask=None, *,
-              costs=True, weights=True, U_upd=True, dmin=False, out=None, stream=None) -> dict:
+              velocity=None, costs=True, weights=True, U_upd=True, dmin=False, out=None, stream=None) -> dict:
     """One EXACT-MPPI control cycle (Algorithm 1).  U is updated in place
     (shifted, or reset to zero when validation fails).  Returns a dict of
     device tensors: u_star, valid, and the requested costs / weights /
-    U_upd / dmin."""
+    U_upd / dmin.  `velocity` (N x 2, m/s) switches to time-indexed
+    obstacle predictions (mppi_step_predicted): step h sees o + t_h v."""
     torch = _torch()
     p = params if isinstance(params, MppiParams) else MppiParams.from_dict(params)
     K, T, nu = p.K, p.T, p.n_u
@@ -308,6 +312,8 @@ def mppi_step(ctx: Context, state, cloud, waypoints, U, noise, footprint: Footpr
     N = cloud.shape[0] if cloud.numel() else 0
     if mask is not None:
         mask = _dev(mask, "mask", torch.uint8, (N,))
+    if velocity is not None:
+        velocity = _dev(velocity, "velocity", torch.float32, (N, 2) if N else None)
     dev = U.device
     o = dict(out or {})
     if "u_star" not in o:
@@ -322,10 +328,17 @@ def mppi_step(ctx: Context, state, cloud, waypoints, U, noise, footprint: Footpr
         o["U_upd"] = torch.empty((T, nu), dtype=torch.float32, device=dev)
     if dmin and "dmin" not in o:
         o["dmin"] = torch.empty((K, T), dtype=torch.float32, device=dev)
-    _check(load().mppi_step(ctx.handle, _ptr(state), _ptr(cloud) if N else None, _ptr(mask), N,
-                            _ptr(waypoints), W, _ptr(U), _ptr(noise), footprint.handle, ctypes.byref(p),
-                            _ptr(o["u_star"]), _ptr(o.get("costs")), _ptr(o.get("weights")), _ptr(o["valid"]),
-                            _ptr(o.get("U_upd")), _ptr(o.get("dmin")), _stream(stream)), "mppi_step")
+    tail = (_ptr(o["u_star"]), _ptr(o.get("costs")), _ptr(o.get("weights")), _ptr(o["valid"]),
+            _ptr(o.get("U_upd")), _ptr(o.get("dmin")), _stream(stream))
+    if velocity is None:
+        _check(load().mppi_step(ctx.handle, _ptr(state), _ptr(cloud) if N else None, _ptr(mask), N,
+                                _ptr(waypoints), W, _ptr(U), _ptr(noise), footprint.handle, ctypes.byref(p), *tail),
+               "mppi_step")
+    else:
+        _check(load().mppi_step_predicted(ctx.handle, _ptr(state), _ptr(cloud) if N else None,
+                                          _ptr(velocity) if N else None, _ptr(mask), N, _ptr(waypoints), W, _ptr(U),
+                                          _ptr(noise), footprint.handle, ctypes.byref(p), *tail),
+               "mppi_step_predicted")
     return o
 
 

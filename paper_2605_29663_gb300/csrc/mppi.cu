@@ -19,54 +19,12 @@
 // The footprint constants are kernel parameters (compile-time edge count).
 // No K x T x N intermediate exists; scratch is per-sample J~ / weights,
 // per-block partial sums and per-step nominal data in the context arena.
-#include "mppi_cycle.cuh"
+#include "mppi_kernels.cuh"
 
 namespace exact {
 
-template <class FPC>
-__global__ void __launch_bounds__(kBlock)
-mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev) {
-    extern __shared__ float2 s_pts[];   // min(N, kStage) staged points
-    __shared__ SampleSmem sm;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        // the validation kernel that follows on the stream counts its
-        // finished blocks on this ticket: start it from zero
-        V.hdr->ticket[1] = 0u;
-        V.hdr->bad = 0;
-    }
-    sample_body(V, ev, blockIdx.x / V.parts, blockIdx.x % V.parts, sm, s_pts, false, 4);
-}
-
-__global__ void __launch_bounds__(kUpdBlock) mppi_update_kernel(const SceneView V) {
-    __shared__ UpdateSmem sm;
-    update_body(V, blockIdx.x, sm);
-}
-
-template <class FPC>
-__global__ void __launch_bounds__(kBlock) mppi_validate_kernel(const SceneView V, const ConstEval<FPC> ev) {
-    __shared__ ValidateSmem sm;
-    validate_body(V, ev, blockIdx.x / V.val_chunks, blockIdx.x % V.val_chunks, sm);
-}
-
 static int parts_of(const exact_ctx *ctx, int K, int T) {
     return parts_for(K, T, ctx->sm_count > 0 ? ctx->sm_count : 148);
-}
-
-// Launch with the programmatic-serialization attribute (see grid_dep_wait).
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
-                                    cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 int check_params(const exact_mppi_params *p) {
@@ -105,13 +63,15 @@ extern "C" int exact_ctx_reserve(exact_ctx *ctx, int max_poses, int max_K, int m
     return ensure_scratch(ctx, need);
 }
 
-extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint8_t *mask,
-                         int n_points, const float *waypoints, int n_wp, float *U, const float *noise,
-                         const exact_footprint *fp, const exact_mppi_params *params,
-                         float *u_star, float *costs, float *weights, int *valid, float *U_upd,
-                         float *dmin, void *stream) {
+namespace exact {
+
+int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const float *velocity,
+                   const uint8_t *mask, int n_points, const float *waypoints, int n_wp, float *U,
+                   const float *noise, const exact_footprint *fp, const exact_mppi_params *params, float *u_star,
+                   float *costs, float *weights, int *valid, float *U_upd, float *dmin, void *stream) {
     if (!ctx || !fp || !state || !U || !noise || !waypoints || n_wp < 1 || n_points < 0) return EXACT_EINVAL;
     if (n_points > 0 && (!cloud || ((uintptr_t)cloud & 7u) != 0)) return EXACT_EINVAL;
+    if (n_points > 0 && velocity && ((uintptr_t)velocity & 7u) != 0) return EXACT_EINVAL;
     int rc = check_params(params);
     if (rc != EXACT_OK) return rc;
     const MppiP P = to_device_params(params);
@@ -122,6 +82,7 @@ extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud,
     V.P = P;
     V.state = state;
     V.pts = reinterpret_cast<const float2 *>(cloud);
+    V.vel = n_points > 0 ? reinterpret_cast<const float2 *>(velocity) : nullptr;
     V.mask = mask;
     V.N = n_points;
     V.wp = waypoints;
@@ -143,36 +104,21 @@ extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud,
         if (cudaMemsetAsync(V.tk, 0, (size_t)P.K * sizeof(unsigned), st) != cudaSuccess) return EXACT_ECUDA;
     }
     ctx->mppi_layout = layout;
-    const size_t smem = (size_t)min(n_points, kStage) * sizeof(float2);
-    return with_footprint(fp, [&](auto fpc) -> int {
-        using FPC = decltype(fpc);
-        const ConstEval<FPC> ev{fpc};
-        mppi_sample_kernel<FPC><<<P.K * V.parts, kBlock, smem, st>>>(V, ev);
-        if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
-        if (launch_dependent(mppi_update_kernel, V.upd_blocks, kUpdBlock, 0, st, V) != cudaSuccess) return EXACT_ECUDA;
-        if (launch_dependent(mppi_validate_kernel<FPC>, P.T * V.val_chunks, kBlock, 0, st, V, ev) != cudaSuccess)
-            return EXACT_ECUDA;
-        return EXACT_OK;
-    });
+    return launch_cycle(V, fp, st);
 }
 
-namespace exact {
-
-// The three launches of one cycle for a scene whose scratch the caller has
-// already carved (the allocation-free entry point's path; mppi_step keeps
-// its own copy of this sequence).
+// Static clouds here; clouds with point velocities in mppi_predicted.cu.
 int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st) {
-    const size_t smem = (size_t)min(V.N, kStage) * sizeof(float2);
-    return with_footprint(fp, [&](auto fpc) -> int {
-        using FPC = decltype(fpc);
-        const ConstEval<FPC> ev{fpc};
-        mppi_sample_kernel<FPC><<<V.P.K * V.parts, kBlock, smem, st>>>(V, ev);
-        if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
-        if (launch_dependent(mppi_update_kernel, V.upd_blocks, kUpdBlock, 0, st, V) != cudaSuccess) return EXACT_ECUDA;
-        if (launch_dependent(mppi_validate_kernel<FPC>, V.P.T * V.val_chunks, kBlock, 0, st, V, ev) != cudaSuccess)
-            return EXACT_ECUDA;
-        return EXACT_OK;
-    });
+    return V.vel ? launch_cycle_moving(V, fp, st) : launch_cycle_t<false>(V, fp, st);
 }
 
 }  // namespace exact
+
+extern "C" int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint8_t *mask,
+                         int n_points, const float *waypoints, int n_wp, float *U, const float *noise,
+                         const exact_footprint *fp, const exact_mppi_params *params,
+                         float *u_star, float *costs, float *weights, int *valid, float *U_upd,
+                         float *dmin, void *stream) {
+    return exact::mppi_step_impl(ctx, state, cloud, nullptr, mask, n_points, waypoints, n_wp, U, noise, fp, params,
+                                 u_star, costs, weights, valid, U_upd, dmin, stream);
+}

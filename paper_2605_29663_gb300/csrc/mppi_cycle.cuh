@@ -23,6 +23,10 @@ namespace exact {
 constexpr int kUpdBlock = 256;
 constexpr int kUpdTile = 8192;    // floats of noise one update block stages (32 KB)
 constexpr int kStage = 4096;      // obstacle points staged in shared memory per pass
+// Points per pass for static (float2 position) or predicted (float4
+// position + velocity) clouds: both fill the same 32 KB of shared memory.
+template <bool MOVING>
+__host__ __device__ constexpr int stage_points_of() { return MOVING ? kStage / 2 : kStage; }
 constexpr int kValChunkPairs = 1024;
 
 // Everything the phases need about one scene.
@@ -30,6 +34,7 @@ struct SceneView {
     MppiP P;
     const float *state;
     const float2 *pts;
+    const float2 *vel;  // N point velocities (time-indexed prediction), or NULL: static points
     const uint8_t *mask;
     int N;
     const float *wp;
@@ -203,9 +208,14 @@ struct SmemEval {
 // point.  Masked points were staged as NaN, which every evaluator turns into
 // a +inf key (NaN terms are dropped by min, and the canonical NaN has a
 // clear sign bit, so it never toggles the crossing parity).
-template <class EV>
+//
+// MOVING: each staged entry is (o_x, o_y, v_x, v_y) and the point of step h
+// is the constant-velocity prediction o + t_h v at the time t_h = (h + off) dt
+// of the scored state (the time-indexed obstacle prediction of Sec. VI).
+template <bool MOVING = false, class EV>
 __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose, int h0,
-                                               int nh, unsigned *keyh, int pairs_per_lane) {
+                                               int nh, unsigned *keyh, int pairs_per_lane, float dt = 0.f,
+                                               int off = 0) {
     const int npairs = (n + 1) >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int span = 32 * pairs_per_lane;
@@ -215,11 +225,20 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
         const int hh = it / nchunk, c = it - hh * nchunk;
         const int h = h0 + hh;
         const float4 q = pose[h];
+        const float th = (float)(h + off) * dt;
         float best = finf();
         const int jend = min(npairs, (c + 1) * span);
         for (int j = c * span + lane; j < jend; j += 32) {
-            const float2 o0 = pts[2 * j];
-            const float2 o1 = pts[min(2 * j + 1, n - 1)];
+            float2 o0, o1;
+            if constexpr (MOVING) {
+                const float4 *p4 = reinterpret_cast<const float4 *>(pts);
+                const float4 a0 = p4[2 * j], a1 = p4[min(2 * j + 1, n - 1)];
+                o0 = make_float2(fmaf(th, a0.z, a0.x), fmaf(th, a0.w, a0.y));
+                o1 = make_float2(fmaf(th, a1.z, a1.x), fmaf(th, a1.w, a1.y));
+            } else {
+                o0 = pts[2 * j];
+                o1 = pts[min(2 * j + 1, n - 1)];
+            }
             float px0, py0, px1, py1;
             body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
             body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
@@ -233,23 +252,33 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
 }
 
 // Copy points [base, base + n) into shared memory, masked ones as NaN.
-// Eight loads per thread are in flight before the first store.
+// Eight loads per thread are in flight before the first store.  MOVING
+// stages (position, velocity) as one float4 per point.
+template <bool MOVING = false>
 __device__ __forceinline__ void stage_points(float2 *dst, const float2 *__restrict__ pts,
-                                             const uint8_t *__restrict__ mask, int base, int n, int t0, int nt) {
+                                             const float2 *__restrict__ vel, const uint8_t *__restrict__ mask,
+                                             int base, int n, int t0, int nt) {
     const float qnan = __int_as_float(0x7fffffff);
     for (int i0 = t0; i0 < n; i0 += 8 * nt) {
-        float2 p[8];
+        float2 p[8], v[8];
         bool ok[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int i = i0 + k * nt;
             p[k] = i < n ? __ldg(pts + base + i) : make_float2(0.f, 0.f);
+            if constexpr (MOVING) v[k] = i < n ? __ldg(vel + base + i) : make_float2(0.f, 0.f);
             ok[k] = i < n && (!mask || __ldg(mask + base + i));
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int i = i0 + k * nt;
-            if (i < n) dst[i] = ok[k] ? p[k] : make_float2(qnan, qnan);
+            if (i < n) {
+                const float2 q = ok[k] ? p[k] : make_float2(qnan, qnan);
+                if constexpr (MOVING)
+                    reinterpret_cast<float4 *>(dst)[i] = make_float4(q.x, q.y, v[k].x, v[k].y);
+                else
+                    dst[i] = q;
+            }
         }
     }
 }
@@ -276,15 +305,17 @@ struct SampleSmem {
 // last part of the sample (atomic ticket) gathers the others' and forms J~
 // exactly as a single block would (same per-step data, same summation
 // order), so the split never changes a bit of the result.  Ends with a
-// __syncthreads.
-template <class EV>
+// __syncthreads.  MOVING: V.vel holds the points' velocities and every step
+// sees the predicted cloud (see steps_min_keys).
+template <bool MOVING = false, class EV>
 __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, int r, int p, SampleSmem &sm,
                                             float2 *s_pts, bool staged, int pairs_per_lane) {
     const MppiP &P = V.P;
     const int T = P.T, nu = P.nu, N = V.N;
+    constexpr int kS = stage_points_of<MOVING>();
     const int h0 = (p * T) / V.parts, h1 = ((p + 1) * T) / V.parts;
     for (int h = h0 + (int)threadIdx.x; h < h1; h += blockDim.x) sm.key[h] = f2ord(finf());
-    const int n0 = min(N, kStage);
+    const int n0 = min(N, kS);
     if (threadIdx.x < 32) {
         const float *U = V.U;
         const float *eps = V.noise + (size_t)r * T * nu;
@@ -305,16 +336,16 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
         }
         if (lane == 0) sm.term = P.w_term * guidance_dist(R.qTx, R.qTy, V.wp, V.W);
     } else if (!staged) {
-        stage_points(s_pts, V.pts, V.mask, 0, n0, threadIdx.x - 32, blockDim.x - 32);
+        stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, 0, n0, threadIdx.x - 32, blockDim.x - 32);
     }
     __syncthreads();
-    steps_min_keys(ev, s_pts, n0, sm.pose, h0, h1 - h0, sm.key, pairs_per_lane);
-    for (int base = kStage; base < N; base += kStage) {   // clouds larger than the stage
-        const int n = min(kStage, N - base);
+    steps_min_keys<MOVING>(ev, s_pts, n0, sm.pose, h0, h1 - h0, sm.key, pairs_per_lane, P.dt, P.state_offset);
+    for (int base = kS; base < N; base += kS) {   // clouds larger than the stage
+        const int n = min(kS, N - base);
         __syncthreads();
-        stage_points(s_pts, V.pts, V.mask, base, n, threadIdx.x, blockDim.x);
+        stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, base, n, threadIdx.x, blockDim.x);
         __syncthreads();
-        steps_min_keys(ev, s_pts, n, sm.pose, h0, h1 - h0, sm.key, pairs_per_lane);
+        steps_min_keys<MOVING>(ev, s_pts, n, sm.pose, h0, h1 - h0, sm.key, pairs_per_lane, P.dt, P.state_offset);
     }
     grid_dep_release();
     __syncthreads();
@@ -448,7 +479,7 @@ struct ValidateSmem {
 // step (one complemented 32-bit order key per step, atomicMax) and the last
 // block scores the nominal exactly like a sample (Sec. III-E, IV-E; the cost
 // J_m of Algorithm 2) and empties the step keys.
-template <class EV>
+template <bool MOVING = false, class EV>
 __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, int h, int c, ValidateSmem &sm) {
     const MppiP &P = V.P;
     const int K = P.K, T = P.T, nu = P.nu, TN = T * nu, G = V.upd_blocks;
@@ -503,11 +534,17 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
     const int N = V.N;
     const int npairs = (N + 1) >> 1;
     const int pend = min(npairs, (c + 1) * kValChunkPairs);
+    const float th = (float)(h + P.state_offset) * P.dt;   // time of the scored state (MOVING)
     float best = finf();
     for (int j = c * kValChunkPairs + tid; j < pend; j += kBlock) {
         const int i0 = 2 * j, i1 = min(2 * j + 1, N - 1);
-        const float2 o0 = __ldg(V.pts + i0);
-        const float2 o1 = __ldg(V.pts + i1);
+        float2 o0 = __ldg(V.pts + i0);
+        float2 o1 = __ldg(V.pts + i1);
+        if constexpr (MOVING) {
+            const float2 v0 = __ldg(V.vel + i0), v1 = __ldg(V.vel + i1);
+            o0 = make_float2(fmaf(th, v0.x, o0.x), fmaf(th, v0.y, o0.y));
+            o1 = make_float2(fmaf(th, v1.x, o1.x), fmaf(th, v1.y, o1.y));
+        }
         float px0, py0, px1, py1;
         body_frame(o0.x, o0.y, qp.x, qp.y, qp.z, qp.w, px0, py0);
         body_frame(o1.x, o1.y, qp.x, qp.y, qp.z, qp.w, px1, py1);

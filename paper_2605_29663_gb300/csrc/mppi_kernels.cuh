@@ -1,0 +1,81 @@
+// mppi_kernels.cuh -- the three kernels of one single-scene control cycle
+// and their stream-ordered launch, templated on static / predicted
+// (time-indexed) obstacle points.  mppi.cu instantiates the static cycle and
+// mppi_predicted.cu the predicted one, so the two compile in parallel.
+#pragma once
+#include "mppi_cycle.cuh"
+
+namespace exact {
+
+template <class FPC, bool MOVING>
+__global__ void __launch_bounds__(kBlock)
+mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev) {
+    extern __shared__ float2 s_pts[];   // min(N, stage) staged points (float4 each when MOVING)
+    __shared__ SampleSmem sm;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // the validation kernel that follows on the stream counts its
+        // finished blocks on this ticket: start it from zero
+        V.hdr->ticket[1] = 0u;
+        V.hdr->bad = 0;
+    }
+    sample_body<MOVING>(V, ev, blockIdx.x / V.parts, blockIdx.x % V.parts, sm, s_pts, false, 4);
+}
+
+template <bool MOVING>
+__global__ void __launch_bounds__(kUpdBlock) mppi_update_kernel(const SceneView V) {
+    __shared__ UpdateSmem sm;
+    update_body(V, blockIdx.x, sm);
+}
+
+template <class FPC, bool MOVING>
+__global__ void __launch_bounds__(kBlock) mppi_validate_kernel(const SceneView V, const ConstEval<FPC> ev) {
+    __shared__ ValidateSmem sm;
+    validate_body<MOVING>(V, ev, blockIdx.x / V.val_chunks, blockIdx.x % V.val_chunks, sm);
+}
+
+// Launch with the programmatic-serialization attribute (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                             cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// The three launches of one cycle for a scene whose scratch is carved.
+template <bool MOVING>
+int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t st) {
+    const size_t smem = (size_t)min(V.N, stage_points_of<MOVING>()) * (MOVING ? sizeof(float4) : sizeof(float2));
+    return with_footprint(fp, [&](auto fpc) -> int {
+        using FPC = decltype(fpc);
+        const ConstEval<FPC> ev{fpc};
+        mppi_sample_kernel<FPC, MOVING><<<V.P.K * V.parts, kBlock, smem, st>>>(V, ev);
+        if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
+        if (launch_dependent(mppi_update_kernel<MOVING>, V.upd_blocks, kUpdBlock, 0, st, V) != cudaSuccess)
+            return EXACT_ECUDA;
+        if (launch_dependent(mppi_validate_kernel<FPC, MOVING>, V.P.T * V.val_chunks, kBlock, 0, st, V, ev) !=
+            cudaSuccess)
+            return EXACT_ECUDA;
+        return EXACT_OK;
+    });
+}
+
+// Static cycle (mppi.cu) and predicted cycle (mppi_predicted.cu).
+int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st);
+int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st);
+
+// mppi_step with optional point velocities (NULL: static cloud).
+int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const float *velocity,
+                   const uint8_t *mask, int n_points, const float *waypoints, int n_wp, float *U,
+                   const float *noise, const exact_footprint *fp, const exact_mppi_params *params, float *u_star,
+                   float *costs, float *weights, int *valid, float *U_upd, float *dmin, void *stream);
+
+}  // namespace exact

@@ -283,7 +283,9 @@ FORKLIFT_RECTS = np.array([(0.0, 0.0, 0.9, 0.5), (1.5, 0.35, 0.6, 0.075), (1.5, 
 
 
 @pytest.mark.parametrize("rects,outline", [(FORKLIFT_RECTS, FORKLIFT_OUTLINE),
-                                           (T_RECTS, T_OUTLINE)])
+                                           (T_RECTS, T_OUTLINE)]
+                         + [(r, o)
+                            for o, r in synth.rectilinear_shapes().values()])
 def test_rect_cover_vs_polygon_outline(rects, outline):
     """Sec. IV-C exactness statement: equal outside, same sign, interior rect >= poly."""
     g = np.random.default_rng(12)

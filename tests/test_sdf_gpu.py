@@ -209,3 +209,26 @@ def test_full_size_microbench_sampled_rows(ex):
     check(w["points"], w["poses"], w["kind"], w["fp"], dg, mg, ag, rows=rows)
     np.testing.assert_array_equal(mg, dg.min(axis=1))
     np.testing.assert_array_equal(dg[np.arange(dg.shape[0]), ag], mg)
+
+
+@pytest.mark.parametrize("shape", ["L", "T", "F"])
+def test_rect_cover_vs_polygon_on_rectilinear_bodies(ex, shape):
+    """Experiment 1's rectilinear bodies evaluated both ways on the GPU: each
+    route matches the oracle, and the two routes agree as the exactness
+    statement of Sec. IV-C says (equal outside the body, same inside flag
+    away from the boundary, rect-cover value >= polygon value inside)."""
+    poly, rects = synth.rectilinear_shapes()[shape]
+    g = np.random.default_rng(31)
+    pts = np.concatenate([g.uniform(-25.0, 25.0, size=(3000, 2)), g.uniform(-1.5, 1.5, size=(3000, 2))])
+    poses = _poses(g, 24, half=2.0)
+    dr, mr, ar = run_gpu(ex, pts, poses, synth.RECTS, rects)
+    dp, mp, ap = run_gpu(ex, pts, poses, synth.POLYGON, poly)
+    check(pts, poses, synth.RECTS, rects.astype(np.float32), dr, mr, ar)
+    check(pts, poses, synth.POLYGON, poly.astype(np.float32), dp, mp, ap)
+    off = np.abs(dp) >= BAND
+    np.testing.assert_array_equal((dr < 0)[off], (dp < 0)[off])
+    out = dp >= BAND
+    assert np.abs(dr[out] - dp[out]).max() <= 2 * TOL
+    ins = dp <= -BAND
+    assert np.all(dr[ins] >= dp[ins] - 2 * TOL)
+    assert ins.sum() > 1000
