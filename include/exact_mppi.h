@@ -297,7 +297,10 @@ int mppi_step_batched(exact_batch *batch, void *stream);
 
 /* Tile autotuner: times the batch's sample phase (which writes only batch
  * scratch, never the scenes' U or outputs) for each candidate tile shape
- * (threads per block x point pairs per lane per work item), `iters` runs
+ * (threads per block x point pairs per lane: the sample phase cuts the
+ * staged cloud into sub-chunks of 64 x pairs_per_lane points, the unit it
+ * skips when a sub-chunk cannot come within d_safe of the footprint at a
+ * step; scenes without a d_min output only), `iters` runs
  * each, keeps the fastest for later steps and, when json_out is non-NULL,
  * writes the timings as JSON text (at most json_cap bytes, NUL-terminated).
  * Synchronises `stream`. */

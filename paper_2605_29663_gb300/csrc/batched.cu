@@ -40,6 +40,7 @@ constexpr size_t kHdrStride = 64;                            // bytes between sc
 struct SceneDev {
     SceneView V;
     int kind, nfp;
+    float3 bc;    // footprint bounding circle
     float4 fpc[kFpSlots];
 };
 
@@ -69,7 +70,7 @@ batched_sample_kernel(const SceneDev *__restrict__ scenes, const int2 *__restric
             __syncthreads();
             fp_scene = it.x;
         }
-        const SmemEval ev{s_fp, D.kind, D.nfp};
+        const SmemEval ev{s_fp, D.kind, D.nfp, D.bc};
         sample_body(D.V, ev, it.y, 0, sm, s_pts, it.x == pts_scene, pairs_per_lane);
         pts_scene = D.V.N <= kStage ? it.x : -1;
     }
@@ -90,7 +91,7 @@ batched_validate_kernel(const SceneDev *__restrict__ scenes, const int2 *__restr
     const SceneDev &D = scenes[t.x];
     load_fp(s_fp, D);
     __syncthreads();
-    const SmemEval ev{s_fp, D.kind, D.nfp};
+    const SmemEval ev{s_fp, D.kind, D.nfp, D.bc};
     validate_body(D.V, ev, t.y / D.V.val_chunks, t.y % D.V.val_chunks, sm);
 }
 
@@ -112,7 +113,7 @@ struct exact_batch {
     size_t ctrl_bytes = 0;
     unsigned *d_queue = nullptr;
     size_t smem = 0;
-    int threads = kBlock, pairs = 4, sms = 0, grid = 0;
+    int threads = kBlock, pairs = 1, sms = 0, grid = 0;
 };
 
 static int batch_grid(exact_batch *b) {
@@ -211,6 +212,7 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         const exact_footprint *fp = S.fp;
         D.kind = fp->kind;
         D.nfp = fp->n_pad;
+        D.bc = make_float3(fp->bcx, fp->bcy, fp->brad);
         if (fp->kind == EXACT_FP_POLYGON) {
             for (int e = 0; e < fp->n_pad; ++e) {
                 D.fpc[2 * e] = make_float4(fp->vx[e], fp->vy[e], fp->exn[e], fp->eyn[e]);

@@ -28,12 +28,14 @@ struct PolyC {
     float exn[E], eyn[E];   // e_b / |e_b|^2   (0 for a zero-length edge)
     float ex[E], ey[E];     // e_b = v_{b+1} - v_b
     float kx[E];            // e_bx / e_by      (0 when e_by == 0)
+    float bcx, bcy, brad;   // bounding circle: centre, radius (rounded up)
 };
 
 // Rectangle cover (Sec. IV-B.1) padded to R boxes by repeating box 0.
 template <int R>
 struct RectC {
     float cx[R], cy[R], sx[R], sy[R];
+    float bcx, bcy, brad;   // bounding circle: centre, radius (rounded up)
 };
 
 // ---------------------------------------------------------------- transform

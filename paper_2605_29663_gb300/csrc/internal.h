@@ -19,6 +19,7 @@ struct exact_footprint {
     float ex[EXACT_MAX_POLY_VERTICES], ey[EXACT_MAX_POLY_VERTICES];
     float kx[EXACT_MAX_POLY_VERTICES];
     float cx[EXACT_MAX_RECTS], cy[EXACT_MAX_RECTS], sx[EXACT_MAX_RECTS], sy[EXACT_MAX_RECTS];
+    float bcx, bcy, brad;   // bounding circle (body frame), radius rounded up
 };
 
 struct exact_ctx {
@@ -59,6 +60,7 @@ inline PolyC<E> make_poly(const exact_footprint *fp) {
         P.ex[b] = fp->ex[b]; P.ey[b] = fp->ey[b];
         P.kx[b] = fp->kx[b];
     }
+    P.bcx = fp->bcx; P.bcy = fp->bcy; P.brad = fp->brad;
     return P;
 }
 
@@ -68,6 +70,7 @@ inline RectC<R> make_rect(const exact_footprint *fp) {
     for (int j = 0; j < R; ++j) {
         Q.cx[j] = fp->cx[j]; Q.cy[j] = fp->cy[j]; Q.sx[j] = fp->sx[j]; Q.sy[j] = fp->sy[j];
     }
+    Q.bcx = fp->bcx; Q.bcy = fp->bcy; Q.brad = fp->brad;
     return Q;
 }
 

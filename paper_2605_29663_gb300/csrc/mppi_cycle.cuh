@@ -136,6 +136,7 @@ struct ConstEval {            // footprint constants in the kernel parameters
         exact::eval2(f, px0, py0, px1, py1, k0, k1);
     }
     __device__ __forceinline__ float dist(float key) const { return key_to_dist(f, key); }
+    __device__ __forceinline__ float3 bound() const { return make_float3(f.bcx, f.bcy, f.brad); }
 };
 
 // Footprint constants in shared memory with a run-time edge / box count.
@@ -147,6 +148,8 @@ struct ConstEval {            // footprint constants in the kernel parameters
 struct SmemEval {
     const float4 *C;
     int kind, n;
+    float3 bc;    // bounding circle of the footprint (centre, radius)
+    __device__ __forceinline__ float3 bound() const { return bc; }
     __device__ __forceinline__ void eval2(float px0, float py0, float px1, float py1, float &k0, float &k1) const {
         if (kind == EXACT_FP_POLYGON) {
             float4 c = C[0];
@@ -199,36 +202,186 @@ struct SmemEval {
     }
 };
 
+// ---------------------------------------------------------------- chunk bounds
+// The staged points are cut into sub-chunks of 64 * ppl consecutive points
+// (ppl pairs per lane of a warp).  For each, circ = (centre, radius, max
+// speed) of its valid points (radius -1 when it has none).
+constexpr int kSub = 64;
+constexpr float kPruneSlack = 1e-3f;   // m: far above the float rounding of the distances
+constexpr int kPruneMin = 1024;        // points: smaller clouds skip the pruning phases
+
+template <bool MOVING>
+__device__ __forceinline__ void chunk_circles(const float2 *pts, int n, float4 *circ, int ppl) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int sz = kSub * ppl;
+    const int nsub = (n + sz - 1) / sz;
+    for (int s = warp; s < nsub; s += nwarps) {
+        float lx = finf(), ly = finf(), hx = -finf(), hy = -finf(), v2 = 0.f;
+        for (int i = s * sz + lane; i < min(n, (s + 1) * sz); i += 32) {
+            float x, y;
+            if constexpr (MOVING) {
+                const float4 a = reinterpret_cast<const float4 *>(pts)[i];
+                x = a.x; y = a.y;
+                if (a.x == a.x) v2 = fmaxf(v2, fmaf(a.z, a.z, a.w * a.w));
+            } else {
+                x = pts[i].x; y = pts[i].y;
+            }
+            lx = fminf(lx, x); hx = fmaxf(hx, x); ly = fminf(ly, y); hy = fmaxf(hy, y);   // NaN (masked) ignored
+        }
+        lx = warp_min_f(lx); ly = warp_min_f(ly); hx = -warp_min_f(-hx); hy = -warp_min_f(-hy);
+        const bool any = lx <= hx;
+        const float cx = 0.5f * (lx + hx), cy = 0.5f * (ly + hy);
+        float r2 = 0.f;
+        for (int i = s * sz + lane; i < min(n, (s + 1) * sz); i += 32) {
+            float x, y;
+            if constexpr (MOVING) {
+                const float4 a = reinterpret_cast<const float4 *>(pts)[i];
+                x = a.x; y = a.y;
+            } else {
+                x = pts[i].x; y = pts[i].y;
+            }
+            if (x == x) r2 = fmaxf(r2, fmaf(x - cx, x - cx, (y - cy) * (y - cy)));
+        }
+        r2 = -warp_min_f(-r2);
+        if (MOVING) v2 = -warp_min_f(-v2);
+        if (lane == 0)
+            circ[s] = any ? make_float4(cx, cy, sqrtf(r2) * 1.000001f, MOVING ? sqrtf(v2) * 1.000001f : 0.f)
+                          : make_float4(0.f, 0.f, -1.f, 0.f);
+    }
+}
+
 // ---------------------------------------------------------------- sample phase
-// Per-step minimum of the body-frame key over n staged points for the T
-// poses in shared memory.  Work items (step h, chunk of 32 * pairs_per_lane
-// point pairs) are dealt to the block's warps round-robin; each item ends
-// in one warp shuffle-min and one shared-memory atomicMin on the
-// order-preserving key of step h.  A ragged last pair repeats its first
-// point.  Masked points were staged as NaN, which every evaluator turns into
-// a +inf key (NaN terms are dropped by min, and the canonical NaN has a
-// clear sign bit, so it never toggles the crossing parity).
+// Per-step minimum of the body-frame key over n staged points for the steps
+// [h0, h0 + nh) whose poses are in shared memory.  Masked points were staged
+// as NaN, which every evaluator turns into a +inf key (NaN terms are dropped
+// by min, and the canonical NaN has a clear sign bit, so it never toggles the
+// crossing parity).  A ragged last pair repeats its first point.
 //
 // MOVING: each staged entry is (o_x, o_y, v_x, v_y) and the point of step h
-// is the constant-velocity prediction o + t_h v at the time t_h = (h + off) dt
-// of the scored state (the time-indexed obstacle prediction of Sec. VI).
+// is the constant-velocity prediction o + t_h v at the time t_h of the scored
+// state (the time-indexed obstacle prediction of Sec. VI).
+//
+// Schedule, in three block-wide phases:
+//  1. one lane per (step, sub-chunk): keep the pair unless the sub-chunk's
+//     circle lies farther than `cap` (plus a slack far above rounding) from
+//     the footprint's bounding circle at that step (cw) -- only when cap >= 0;
+//  2. a prefix sum of the kept pairs per step (bit masks in msk);
+//  3. every warp evaluates an equal contiguous share of the kept (step,
+//     sub-chunk) list and folds each step's minimum into keyh[h] (one warp
+//     shuffle-min and one shared atomicMin per step run).
+// Pruning never changes a result: cap = d_safe is passed only when no d_min
+// output is wanted, and every cost term and the validation test are the same
+// for any d >= d_safe; a skipped point is provably farther than that.
+// Without pruning (cap < 0) the three phases are replaced by items (step h,
+// chunk of 128 pairs) dealt to the warps round-robin, each ending in one
+// warp shuffle-min and one shared atomicMin on the key of step h.
 template <bool MOVING = false, class EV>
-__device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose, int h0,
-                                               int nh, unsigned *keyh, int pairs_per_lane, float dt = 0.f,
-                                               int off = 0) {
+__device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose,
+                                               const float4 *cw, int h0, int nh, unsigned *keyh, int ppl,
+                                               const float4 *circ, float cap, unsigned *msk, int *pre) {
     const int npairs = (n + 1) >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int span = 32 * pairs_per_lane;
-    const int nchunk = npairs > 0 ? (npairs + span - 1) / span : 0;
-    const int items = nh * nchunk;
-    for (int it = warp; it < items; it += nwarps) {
-        const int hh = it / nchunk, c = it - hh * nchunk;
+    const int nsub = (n + kSub * ppl - 1) / (kSub * ppl);
+    if (cap < 0.f) {
+        const int span = 32 * 4;   // pairs per item
+        const int nchunk = npairs > 0 ? (npairs + span - 1) / span : 0;
+        const int items = nh * nchunk;
+        for (int it = warp; it < items; it += nwarps) {
+            const int hh = it / nchunk, c = it - hh * nchunk;
+            const int h = h0 + hh;
+            const float4 q = pose[h];
+            const float th = cw[h].z;
+            float best = finf();
+            const int jend = min(npairs, (c + 1) * span);
+            for (int j = c * span + lane; j < jend; j += 32) {
+                float2 o0, o1;
+                if constexpr (MOVING) {
+                    const float4 *p4 = reinterpret_cast<const float4 *>(pts);
+                    const float4 a0 = p4[2 * j], a1 = p4[min(2 * j + 1, n - 1)];
+                    o0 = make_float2(fmaf(th, a0.z, a0.x), fmaf(th, a0.w, a0.y));
+                    o1 = make_float2(fmaf(th, a1.z, a1.x), fmaf(th, a1.w, a1.y));
+                } else {
+                    o0 = pts[2 * j];
+                    o1 = pts[min(2 * j + 1, n - 1)];
+                }
+                float px0, py0, px1, py1;
+                body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
+                body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
+                float k0, k1;
+                ev.eval2(px0, py0, px1, py1, k0, k1);
+                best = fmin3(best, k0, k1);
+            }
+            best = warp_min_f(best);
+            if (lane == 0) atomicMin(keyh + h, f2ord(best));
+        }
+        return;
+    }
+    const float brad = ev.bound().z;
+    const float lim = cap >= 0.f ? cap + kPruneSlack : finf();
+    // 1. per (step, sub-chunk) tests, 32 sub-chunks per ballot
+    for (int idx = warp; idx < 2 * nh; idx += nwarps) {
+        const int hh = idx >> 1, s = ((idx & 1) << 5) + lane;
+        bool keep = false;
+        if (s < nsub) {
+            const float4 cc = circ[s];
+            if (cc.z >= 0.f) {
+                const float4 cq = cw[h0 + hh];
+                const float dx = cc.x - cq.x, dy = cc.y - cq.y;
+                float reach = cc.z + brad + 1e-5f * (fabsf(cc.x) + fabsf(cc.y) + fabsf(cq.x) + fabsf(cq.y));
+                if (MOVING) reach = fmaf(cq.z, cc.w, reach);
+                const float far = reach + lim;   // drop iff |centre - footprint centre| > far
+                keep = !(fmaf(dx, dx, dy * dy) > far * far);
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) msk[idx] = b;
+    }
+    __syncthreads();
+    // 2. exclusive prefix of the per-step counts
+    if (warp == 0) {
+        int run = 0;
+        for (int base = 0; base < nh; base += 32) {
+            const int hh = base + lane;
+            const int cnt = hh < nh ? __popc(msk[2 * hh]) + __popc(msk[2 * hh + 1]) : 0;
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            if (hh < nh) pre[hh] = run + inc - cnt;
+            run += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) pre[nh] = run;
+    }
+    __syncthreads();
+    // 3. this warp's share [e0, e1) of the kept list, in (step, sub-chunk) order
+    const int L = pre[nh];
+    const int e0 = (int)(((long long)L * warp) / nwarps), e1 = (int)(((long long)L * (warp + 1)) / nwarps);
+    if (e0 >= e1) return;
+    int lo = 0, hi = nh - 1;   // the step holding entry e0: the last with pre <= e0
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= e0) lo = mid; else hi = mid - 1;
+    }
+    int hh = lo;
+    unsigned long long m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
+    for (int k = pre[hh]; k < e0; ++k) m &= m - 1ull;
+    float best = finf();
+    for (int e = e0; e < e1; ++e) {
+        while (m == 0ull) {   // step done: fold its minimum, move to the next step with entries
+            best = warp_min_f(best);
+            if (lane == 0 && best < finf()) atomicMin(keyh + h0 + hh, f2ord(best));
+            best = finf();
+            ++hh;
+            m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
+        }
+        const int s = __ffsll((long long)m) - 1;
+        m &= m - 1ull;
         const int h = h0 + hh;
         const float4 q = pose[h];
-        const float th = (float)(h + off) * dt;
-        float best = finf();
-        const int jend = min(npairs, (c + 1) * span);
-        for (int j = c * span + lane; j < jend; j += 32) {
+        const float th = cw[h].z;
+        for (int j = s * 32 * ppl + lane; j < min(npairs, (s + 1) * 32 * ppl); j += 32) {
             float2 o0, o1;
             if constexpr (MOVING) {
                 const float4 *p4 = reinterpret_cast<const float4 *>(pts);
@@ -246,9 +399,9 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
             ev.eval2(px0, py0, px1, py1, k0, k1);
             best = fmin3(best, k0, k1);
         }
-        best = warp_min_f(best);
-        if (lane == 0) atomicMin(keyh + h, f2ord(best));
     }
+    best = warp_min_f(best);
+    if (lane == 0 && best < finf()) atomicMin(keyh + h0 + hh, f2ord(best));
 }
 
 // Copy points [base, base + n) into shared memory, masked ones as NaN.
@@ -291,6 +444,10 @@ __device__ __forceinline__ double phi_obs_d(const MppiP &P, float d) {
 }
 
 struct SampleSmem {
+    float4 circ[kStage / kSub];        // sub-chunk bounding circles
+    float4 cw[EXACT_MAX_HORIZON];      // footprint circle centre (world) and t_h per step
+    unsigned msk[2 * EXACT_MAX_HORIZON];   // kept (step, sub-chunk) pairs, 64 bits per step
+    int pre[EXACT_MAX_HORIZON + 1];        // exclusive prefix of their counts
     float4 pose[EXACT_MAX_HORIZON];
     float stage[EXACT_MAX_HORIZON];
     unsigned key[EXACT_MAX_HORIZON];
@@ -316,6 +473,7 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     const int h0 = (p * T) / V.parts, h1 = ((p + 1) * T) / V.parts;
     for (int h = h0 + (int)threadIdx.x; h < h1; h += blockDim.x) sm.key[h] = f2ord(finf());
     const int n0 = min(N, kS);
+    const float3 bc = ev.bound();
     if (threadIdx.x < 32) {
         const float *U = V.U;
         const float *eps = V.noise + (size_t)r * T * nu;
@@ -330,22 +488,39 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
                 float sn, cs;
                 sincosf(R.th[e], &sn, &cs);
                 sm.pose[h] = make_float4(R.x[e], R.y[e], cs, sn);
+                sm.cw[h] = make_float4(fmaf(cs, bc.x, fmaf(-sn, bc.y, R.x[e])), fmaf(sn, bc.x, fmaf(cs, bc.y, R.y[e])),
+                                       (float)(h + P.state_offset) * P.dt, 0.f);
                 const float u2 = fmaf(R.u[e][0], R.u[e][0], fmaf(R.u[e][1], R.u[e][1], R.u[e][2] * R.u[e][2]));
                 sm.stage[h] = fmaf(P.w_goal, guidance_dist(R.x[e], R.y[e], V.wp, V.W), P.w_ctrl * u2);
             }
         }
         if (lane == 0) sm.term = P.w_term * guidance_dist(R.qTx, R.qTy, V.wp, V.W);
+
     } else if (!staged) {
         stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, 0, n0, threadIdx.x - 32, blockDim.x - 32);
     }
     __syncthreads();
-    steps_min_keys<MOVING>(ev, s_pts, n0, sm.pose, h0, h1 - h0, sm.key, pairs_per_lane, P.dt, P.state_offset);
+    const bool prune = !V.dmin && N >= kPruneMin;
+    if (!staged && prune) {
+        chunk_circles<MOVING>(s_pts, n0, sm.circ, pairs_per_lane);
+        __syncthreads();
+    }
+    // without a d_min output the costs only need min(d_min, d_safe); clouds
+    // of fewer than kPruneMin points are not worth the pruning phases
+    const float cap = V.dmin || N < kPruneMin ? -1.f : fmaxf(P.d_safe, 0.f);
+    steps_min_keys<MOVING>(ev, s_pts, n0, sm.pose, sm.cw, h0, h1 - h0, sm.key, pairs_per_lane, sm.circ, cap,
+                           sm.msk, sm.pre);
     for (int base = kS; base < N; base += kS) {   // clouds larger than the stage
         const int n = min(kS, N - base);
         __syncthreads();
         stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, base, n, threadIdx.x, blockDim.x);
         __syncthreads();
-        steps_min_keys<MOVING>(ev, s_pts, n, sm.pose, h0, h1 - h0, sm.key, pairs_per_lane, P.dt, P.state_offset);
+        if (prune) {
+            chunk_circles<MOVING>(s_pts, n, sm.circ, pairs_per_lane);
+            __syncthreads();
+        }
+        steps_min_keys<MOVING>(ev, s_pts, n, sm.pose, sm.cw, h0, h1 - h0, sm.key, pairs_per_lane, sm.circ, cap,
+                               sm.msk, sm.pre);
     }
     grid_dep_release();
     __syncthreads();

@@ -18,7 +18,7 @@ mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev) {
         V.hdr->ticket[1] = 0u;
         V.hdr->bad = 0;
     }
-    sample_body<MOVING>(V, ev, blockIdx.x / V.parts, blockIdx.x % V.parts, sm, s_pts, false, 4);
+    sample_body<MOVING>(V, ev, blockIdx.x / V.parts, blockIdx.x % V.parts, sm, s_pts, false, 1);
 }
 
 template <bool MOVING>

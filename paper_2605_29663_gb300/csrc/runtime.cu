@@ -147,6 +147,31 @@ extern "C" int exact_footprint_create(int kind, const float *host_data, int n, e
             fp->sy[j] = host_data[4 * s + 3];
         }
     }
+    // bounding circle of the footprint (centre of the bounding box, largest
+    // vertex / box-corner distance), rounded outwards, for the bound that
+    // lets the MPPI kernels skip far point chunks
+    double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+    auto corners = [&](auto &&visit) {
+        if (kind == EXACT_FP_POLYGON) {
+            for (int b = 0; b < n; ++b) visit((double)host_data[2 * b], (double)host_data[2 * b + 1]);
+        } else {
+            for (int j = 0; j < n; ++j)
+                for (int sx = -1; sx <= 1; sx += 2)
+                    for (int sy = -1; sy <= 1; sy += 2)
+                        visit((double)host_data[4 * j] + sx * (double)host_data[4 * j + 2],
+                              (double)host_data[4 * j + 1] + sy * (double)host_data[4 * j + 3]);
+        }
+    };
+    corners([&](double x, double y) {
+        lo[0] = fmin(lo[0], x); lo[1] = fmin(lo[1], y);
+        hi[0] = fmax(hi[0], x); hi[1] = fmax(hi[1], y);
+    });
+    const double bcx = 0.5 * (lo[0] + hi[0]), bcy = 0.5 * (lo[1] + hi[1]);
+    double r2 = 0.0;
+    corners([&](double x, double y) { r2 = fmax(r2, (x - bcx) * (x - bcx) + (y - bcy) * (y - bcy)); });
+    fp->bcx = (float)bcx;
+    fp->bcy = (float)bcy;
+    fp->brad = (float)(sqrt(r2) * (1.0 + 1e-6) + 1e-6 + fabs((double)fp->bcx - bcx) + fabs((double)fp->bcy - bcy));
     *out = fp;
     return EXACT_OK;
 }

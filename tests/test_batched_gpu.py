@@ -125,3 +125,21 @@ def test_batch_rejects_bad_scene(ex):
     d["params"] = dict(s["params"], **{"lambda": 0.0})   # the temperature must be positive
     with pytest.raises(ex.ExactError):
         ex.Batch([d])
+
+
+def test_batched_pruning_changes_no_cost(ex):
+    """A batch without d_min outputs prunes point chunks beyond d_safe: same
+    J~, weights and sequences as the batch that outputs d_min, bit for bit."""
+    import torch
+    scenes = _scene_set(5, 8, 0.05)
+    res = []
+    for dmin in (True, False):
+        dev = [_dev_scene(ex, s) for s in scenes]
+        b = ex.Batch(dev, dmin=dmin)
+        b.step()
+        torch.cuda.synchronize()
+        res.append([dict({k: v.cpu().numpy() for k, v in o.items()}, U=d["U"].cpu().numpy())
+                    for d, o in zip(dev, b.outputs)])
+    for i in range(len(scenes)):
+        for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
+            np.testing.assert_array_equal(res[0][i][k], res[1][i][k], err_msg=f"scene {i} {k}")

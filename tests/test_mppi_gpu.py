@@ -232,3 +232,27 @@ def test_context_reused_across_shapes_and_entry_points(ex):
         ex.sdf_batch(pts, torch.zeros((2, 3), device="cuda"), ex.Footprint(s["kind"], s["fp"]), ctx=shared,
                      dist=False)
         torch.cuda.synchronize()
+
+
+def _pruning_cases():
+    yield "plain", synth.plain_step(40)
+    yield "forklift", synth.forklift(41, K=512, T=30, N=4096)
+    s = synth.dynamic_scene(42, K=256, T=20, N=2048)
+    s.pop("vel")
+    yield "boxes_and_discs", s
+    yield "hybrid_ackermann", synth.hybrid(43, K=256, T=20, N=2048)[0]
+    yield "batched_scene", synth.batched(44, n_scenes=1, scale=0.25)[0]
+
+
+@pytest.mark.parametrize("case", list(range(5)))
+def test_far_chunk_pruning_changes_no_cost(ex, ctx, case):
+    """Without a d_min output the sample kernel skips point chunks farther than
+    d_safe from the footprint; with it, only chunks farther than the current
+    minimum.  Both must give the same J~, weights and updated sequences bit for
+    bit (every cost term is constant for d >= d_safe)."""
+    name, s = list(_pruning_cases())[case]
+    a = run_gpu(ex, ctx, s, dmin=True)
+    b = run_gpu(ex, ctx, s, dmin=False)
+    for k in ("costs", "weights", "U_upd", "U", "u_star"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=f"{name} {k}")
+    assert a["valid"] == b["valid"]

@@ -119,3 +119,20 @@ def test_missing_velocity_is_rejected(ex, ctx):
                                        fp.handle, ctypes.byref(p), u.data_ptr(), None, None, None, None, None,
                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 1   # EXACT_EINVAL, before any launch
+
+
+def test_pruning_with_predictions_changes_no_cost(ex, ctx):
+    """Predicted clouds prune with circles grown by t_h * max speed: the run
+    without d_min output equals the run with it bit for bit."""
+    import torch
+    s = synth.dynamic_scene(9, K=384, T=24, N=2048, speed=1.5)
+    res = []
+    for dmin in (True, False):
+        fp = ex.Footprint(s["kind"], s["fp"])
+        U = _t(s["U"].astype(np.float32))
+        out = ex.mppi_step(ctx, _t(s["q0"]), _t(s["cloud"]), _t(s["waypoints"]), U, _t(s["eps"]), fp, s["params"],
+                           mask=None if s["mask"] is None else _t(s["mask"]), velocity=_t(s["vel"]), dmin=dmin)
+        torch.cuda.synchronize()
+        res.append(dict({k: v.cpu().numpy() for k, v in out.items()}, U=U.cpu().numpy()))
+    for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
+        np.testing.assert_array_equal(res[0][k], res[1][k], err_msg=k)
