@@ -156,23 +156,32 @@ struct SmemEval {
             float dxa0 = px0 - c.x, dya0 = py0 - c.y, dxa1 = px1 - c.x, dya1 = py1 - c.y;
             float m0 = finf(), m1 = finf();
             unsigned s0 = 0u, s1 = 0u;
-#pragma unroll 2
-            for (int b = 0; b < n; ++b) {
-                const float4 e = C[2 * b + 1];
-                const float4 nx = C[2 * b + 2];
+            // one edge for both points: squared segment distances, parity
+            // toggles, and the differences advanced to the next vertex
+            auto edge = [&](const float4 &e, const float4 &nx, float &q0, float &q1) {
                 const float dxb0 = px0 - nx.x, dyb0 = py0 - nx.y, dxb1 = px1 - nx.x, dyb1 = py1 - nx.y;
                 const float t0 = __saturatef(fmaf(dya0, c.w, dxa0 * c.z));
                 const float t1 = __saturatef(fmaf(dya1, c.w, dxa1 * c.z));
                 const float qx0 = fmaf(-t0, e.x, dxa0), qy0 = fmaf(-t0, e.y, dya0);
                 const float qx1 = fmaf(-t1, e.x, dxa1), qy1 = fmaf(-t1, e.y, dya1);
-                m0 = fminf(m0, fmaf(qy0, qy0, qx0 * qx0));
-                m1 = fminf(m1, fmaf(qy1, qy1, qx1 * qx1));
+                q0 = fmaf(qy0, qy0, qx0 * qx0);
+                q1 = fmaf(qy1, qy1, qx1 * qx1);
                 const float g0 = fmaf(dya0, e.z, -dxa0), g1 = fmaf(dya1, e.z, -dxa1);
                 const float X0 = dya0 * dyb0, X1 = dya1 * dyb1;
                 s0 ^= __float_as_uint(X0) & ~__float_as_uint(g0);
                 s1 ^= __float_as_uint(X1) & ~__float_as_uint(g1);
                 dxa0 = dxb0; dya0 = dyb0; dxa1 = dxb1; dya1 = dyb1;
                 c = nx;
+            };
+            // the edge count is padded to an even number: two edges per
+            // step, folded with one three-input minimum per point
+            for (int b = 0; b < n; b += 2) {
+                const float4 ea = C[2 * b + 1], na = C[2 * b + 2], eb = C[2 * b + 3], nb = C[2 * b + 4];
+                float qa0, qa1, qb0, qb1;
+                edge(ea, na, qa0, qa1);
+                edge(eb, nb, qb0, qb1);
+                m0 = fmin3(m0, qa0, qb0);
+                m1 = fmin3(m1, qa1, qb1);
             }
             k0 = __uint_as_float(__float_as_uint(m0) | (s0 & 0x80000000u));
             k1 = __uint_as_float(__float_as_uint(m1) | (s1 & 0x80000000u));
