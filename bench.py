@@ -44,7 +44,7 @@ L2_BYTES = 129 * 1024 * 1024
 # profiles/sdf_batch_kernel_poly32_16384x8192.md, valid only while the kernel
 # sources hash to the recorded value (reported as null otherwise).
 TRAFFIC = {"sources": ["paper_2605_29663_gb300/csrc/sdf_batch.cu", "paper_2605_29663_gb300/csrc/common.cuh"],
-           "sha256_16": "55dda293bf801ae6", "bytes_per_launch": 350976 + 476276224}
+           "sha256_16": "74c696572c36d89f", "bytes_per_launch": 586496 + 476210688}
 
 
 def measured_traffic():
@@ -494,7 +494,9 @@ def batched_extra(torch, ex, dev, steps=3, tune=True):
 
 
 def run_mppi_workload(args):
-    """Time one MPPI cycle workload (plain_step or forklift) as plain launches."""
+    """Time one MPPI cycle workload on its own, as plain launches (for
+    profiling): plain_step, forklift, predicted (the dynamic scene through
+    mppi_step_predicted), hybrid (three modes) or batched64."""
     import torch
 
     import paper_2605_29663_gb300 as ex
@@ -503,30 +505,60 @@ def run_mppi_workload(args):
     _build.build()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    s = synth.plain_step(0) if args.workload == "plain_step" else synth.forklift(0)
-    p = s["params"]
-    fp = ex.Footprint(s["kind"], s["fp"])
-    t = {k: torch.from_numpy(s[k]).to(dev) for k in ("q0", "cloud", "waypoints", "U", "eps")}
-    mask = torch.from_numpy(s["mask"]).to(dev) if s["mask"] is not None else None
-    ctx = ex.Context()
-    ctx.reserve(0, p["K"], p["T"])
-    outs = {}
+    launches = 3
+    if args.workload in ("plain_step", "forklift", "predicted"):
+        s = {"plain_step": synth.plain_step, "forklift": synth.forklift, "predicted": synth.dynamic_scene}[
+            args.workload](0)
+        p = s["params"]
+        fp = ex.Footprint(s["kind"], s["fp"])
+        t = {k: torch.from_numpy(s[k]).to(dev) for k in ("q0", "cloud", "waypoints", "U", "eps")}
+        vel = torch.from_numpy(s["vel"]).to(dev) if args.workload == "predicted" else None
+        mask = torch.from_numpy(s["mask"]).to(dev) if s["mask"] is not None else None
+        ctx = ex.Context()
+        ctx.reserve(0, p["K"], p["T"])
+        outs = {}
+
+        def step():
+            outs.update(ex.mppi_step(ctx, t["q0"], t["cloud"], t["waypoints"], t["U"], t["eps"], fp, p, mask=mask,
+                                     velocity=vel, out=outs))
+        cfg = {"K": p["K"], "T": p["T"], "N": s["cloud"].shape[0]}
+    elif args.workload == "hybrid":
+        modes = synth.hybrid(0)
+        fp = ex.Footprint(modes[0]["kind"], modes[0]["fp"])
+        sh = {k: torch.from_numpy(modes[0][k]).to(dev) for k in ("q0", "cloud", "waypoints")}
+        devs = [dict(state=sh["q0"], cloud=sh["cloud"], waypoints=sh["waypoints"],
+                     mask=None if m["mask"] is None else torch.from_numpy(m["mask"]).to(dev),
+                     U=torch.from_numpy(m["U"]).to(dev), noise=torch.from_numpy(m["eps"]).to(dev), fp=fp,
+                     params=m["params"]) for m in modes]
+        h = ex.Hybrid(devs, lambda_switch=2.0, cool_max=3)
+        step = h.step
+        launches = 4
+        cfg = {"modes": 3, "K": modes[0]["params"]["K"], "T": modes[0]["params"]["T"], "N": modes[0]["cloud"].shape[0]}
+    else:
+        scenes = synth.batched(0)
+        devs = [dict(state=torch.from_numpy(s["q0"]).to(dev), cloud=torch.from_numpy(s["cloud"]).to(dev),
+                     waypoints=torch.from_numpy(s["waypoints"]).to(dev), U=torch.from_numpy(s["U"]).to(dev),
+                     noise=torch.from_numpy(s["eps"]).to(dev),
+                     mask=None if s["mask"] is None else torch.from_numpy(s["mask"]).to(dev),
+                     fp=ex.Footprint(s["kind"], s["fp"]), params=s["params"]) for s in scenes]
+        b = ex.Batch(devs)
+        step = b.step
+        cfg = {"scenes": len(scenes)}
     for _ in range(args.warmup):
-        outs.update(ex.mppi_step(ctx, t["q0"], t["cloud"], t["waypoints"], t["U"], t["eps"], fp, p, mask=mask,
-                                 out=outs))
+        step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        ex.mppi_step(ctx, t["q0"], t["cloud"], t["waypoints"], t["U"], t["eps"], fp, p, mask=mask, out=outs)
+        step()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     print(json.dumps({"metric": "MPPI steps/s", "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": args.workload, "K": p["K"], "T": p["T"], "N": s["cloud"].shape[0]},
-                      "gpu_launches": 3 * args.steps}), flush=True)
+                      "config": dict({"workload": args.workload}, **cfg),
+                      "gpu_launches": launches * args.steps}), flush=True)
     return 0
 
 
@@ -677,7 +709,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the MPPI cycle measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target length of the CPU oracle sample")
-    ap.add_argument("--workload", choices=["sdf", "plain_step", "forklift"], default="sdf",
+    ap.add_argument("--workload", choices=["sdf", "plain_step", "forklift", "predicted", "hybrid", "batched64"],
+                    default="sdf",
                     help="sdf (headline) or one MPPI cycle workload timed on its own")
     args = ap.parse_args()
     if args.warmup < 3:
