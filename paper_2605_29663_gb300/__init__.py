@@ -352,6 +352,61 @@ class ExactScene(ctypes.Structure):
                 ("dmin", ctypes.c_void_p), ("nom_cost", ctypes.c_void_p)]
 
 
+def scene_class_key(scenes, device: str = "") -> str:
+    """Key of a batch's shape class for the tile cache: the sorted multiset of
+    (footprint kind, footprint size, N rounded up to a power of two, K, T) of
+    its scenes, and the device name.  Batches with the same key are expected
+    to prefer the same tile shape."""
+    import hashlib
+    import json
+    items = []
+    for sc in scenes:
+        fp = sc["fp"]
+        p = sc["params"]
+        K, T = (p.K, p.T) if isinstance(p, MppiParams) else (int(p["K"]), int(p["T"]))
+        N = int(sc["cloud"].shape[0]) if sc["cloud"].numel() else 0
+        items.append([int(fp.kind), int(fp.n), 1 << max(N - 1, 0).bit_length(), K, T])
+    items.sort()
+    blob = json.dumps({"scenes": items, "device": device}, sort_keys=True)
+    return hashlib.sha256(blob.encode()).hexdigest()[:24]
+
+
+def tile_cache_lookup(path: str, key: str):
+    """(threads, pairs_per_lane) stored for `key` in the JSON tile cache, or None."""
+    import json
+    try:
+        with open(path) as fh:
+            e = json.load(fh).get(key)
+    except (OSError, ValueError):
+        return None
+    if not isinstance(e, dict):
+        return None
+    try:
+        return int(e["threads"]), int(e["pairs_per_lane"])
+    except (KeyError, TypeError, ValueError):
+        return None
+
+
+def tile_cache_store(path: str, key: str, threads: int, pairs_per_lane: int, ms: float) -> None:
+    """Record the tuned tile shape for `key` (read-modify-write, atomic rename)."""
+    import json
+    import tempfile
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+        if not isinstance(data, dict):
+            data = {}
+    except (OSError, ValueError):
+        data = {}
+    data[key] = {"threads": int(threads), "pairs_per_lane": int(pairs_per_lane), "ms": float(ms)}
+    d = os.path.dirname(os.path.abspath(path))
+    os.makedirs(d, exist_ok=True)
+    fd, tmp = tempfile.mkstemp(dir=d, prefix=".tiles-", suffix=".json")
+    with os.fdopen(fd, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 def _scene_array(scenes, dmin, costs, weights, U_upd, nom_cost):
     """exact_scene array for a list of scene dicts (see Batch), the output
     tensors allocated for each scene, and the tensors the array points into."""
@@ -413,6 +468,8 @@ class Batch:
 
     def __init__(self, scenes, *, dmin=False, costs=True, weights=True, U_upd=True, nom_cost=False):
         arr, self.outputs, self._keep = _scene_array(scenes, dmin, costs, weights, U_upd, nom_cost)
+        torch = _torch()
+        self.class_key = scene_class_key(scenes, torch.cuda.get_device_name(self.outputs[0]["u_star"].device))
         h = ctypes.c_void_p()
         _check(load().exact_batch_create(len(scenes), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(h)),
                "exact_batch_create")
@@ -422,11 +479,26 @@ class Batch:
     def step(self, stream=None):
         _check(load().mppi_step_batched(self._h, _stream(stream)), "mppi_step_batched")
 
-    def autotune(self, iters: int = 3, stream=None) -> dict:
+    def autotune(self, iters: int = 3, stream=None, cache: str | None = None) -> dict:
+        """Pick the tile shape by timing the candidates (exact_batch_autotune).
+        With `cache` (a JSON file path) a shape already tuned for this batch's
+        shape class (scene_class_key) is reused without timing, and a new
+        result is stored there."""
         import json
+        if cache:
+            hit = tile_cache_lookup(cache, self.class_key)
+            if hit is not None:
+                self.set_tiles(*hit)
+                return {"cached": True, "key": self.class_key,
+                        "best": {"threads": hit[0], "pairs_per_lane": hit[1]}}
         buf = ctypes.create_string_buffer(8192)
         _check(load().exact_batch_autotune(self._h, iters, buf, 8192, _stream(stream)), "exact_batch_autotune")
-        return json.loads(buf.value.decode())
+        rep = json.loads(buf.value.decode())
+        if cache:
+            b = rep["best"]
+            tile_cache_store(cache, self.class_key, b["threads"], b["pairs_per_lane"], b["ms"])
+            rep["key"] = self.class_key
+        return rep
 
     @property
     def tiles(self):

@@ -143,3 +143,17 @@ def test_batched_pruning_changes_no_cost(ex):
     for i in range(len(scenes)):
         for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
             np.testing.assert_array_equal(res[0][i][k], res[1][i][k], err_msg=f"scene {i} {k}")
+
+
+def test_autotune_persists_the_tile_shape(ex, tmp_path):
+    """Tuning with a cache file stores the winner under the batch's shape key;
+    a second batch of the same class reuses it without timing."""
+    scenes = _scene_set(6, 4, 0.05)
+    cache = str(tmp_path / "tiles.json")
+    b1 = ex.Batch([_dev_scene(ex, s) for s in scenes])
+    rep = b1.autotune(iters=1, cache=cache)
+    assert "candidates" in rep and rep["key"] == b1.class_key
+    b2 = ex.Batch([_dev_scene(ex, s) for s in scenes])
+    b2.set_tiles(64, 8)
+    rep2 = b2.autotune(iters=1, cache=cache)
+    assert rep2["cached"] and b2.tiles == b1.tiles
