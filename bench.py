@@ -56,6 +56,22 @@ def measured_traffic():
     return TRAFFIC["bytes_per_launch"] if h.hexdigest()[:16] == TRAFFIC["sha256_16"] else None
 
 
+def max_over_ranks(torch, dist, ms: float, dev) -> float:
+    """The slowest rank's per-step time (every rank returns it); ms itself
+    without a process group."""
+    if dist is None:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, units_per_rank_step: float, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed per step over the
+    slowest rank's step time (weak scaling: every rank runs its own replica)."""
+    return world * units_per_rank_step / (ms * 1e-3)
+
+
 def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
     """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -621,13 +637,9 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(per) / len(per)
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(torch, dist, sum(per) / len(per), dev)
     evals = N_POSES * N_POINTS * N_VERTS
-    value = world * evals / (ms * 1e-3)
+    value = whole_job_value(world, evals, ms)
 
     # end to end through the public call with host buffers: H2D of the step's
     # inputs from pinned memory, the call, D2H of the per-pose min / argmin
