@@ -256,3 +256,42 @@ def test_far_chunk_pruning_changes_no_cost(ex, ctx, case):
     for k in ("costs", "weights", "U_upd", "U", "u_star"):
         np.testing.assert_array_equal(a[k], b[k], err_msg=f"{name} {k}")
     assert a["valid"] == b["valid"]
+
+
+def _coherent_scene(seed, K, T, N, mask_tail=0, n_obst=40):
+    """Obstacle edge points in obstacle order (spatially coherent runs, as a
+    scan delivers them), fitted to N; the last mask_tail points masked."""
+    g = synth.rng(seed)
+    s = synth.random_scene(g, synth.DIFF, 6, N, K, T, n_obst=n_obst)
+    s["fp"] = synth.l_footprint()
+    if mask_tail:
+        m = np.ones(N, np.uint8) if s["mask"] is None else s["mask"].copy()
+        m[N - mask_tail:] = 0
+        s["mask"] = m
+    return s
+
+
+@pytest.mark.parametrize("K,T,N,tail", [(256, 20, 1024, 0), (256, 20, 1024 + 37, 5), (300, 16, 9000, 0),
+                                        (128, 128, 2048, 0), (24, 16, 5000, 3), (512, 12, 4096, 4030)])
+def test_pruning_edge_cases(ex, ctx, K, T, N, tail):
+    """The pruned sample phase at its boundaries: the 1,024-point threshold, a
+    ragged last sub-chunk, several shared-memory passes, the longest horizon,
+    a split horizon (few samples) and sub-chunks with nothing but masked
+    points.  Bitwise against the unpruned run, and against the oracle."""
+    s = _coherent_scene(K + N, K, T, N, mask_tail=tail)
+    a = run_gpu(ex, ctx, s, dmin=True)
+    b = run_gpu(ex, ctx, s, dmin=False)
+    for k in ("costs", "weights", "U_upd", "U", "u_star"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    o = run_oracle(s)
+    if o["n_near"] == 0:
+        compare(s, b, o, check_dmin=False)
+
+
+def test_largest_sample_count(ex, ctx):
+    """K = 65,536 (the largest accepted) against the oracle."""
+    s = synth.plain_step(77, K=65536, T=6, N=96)
+    o = run_oracle(s)
+    if o["n_near"]:
+        pytest.skip("threshold-adjacent d_min in this seed")
+    compare(s, run_gpu(ex, ctx, s), o)
