@@ -3,7 +3,8 @@
 //   mppi_sample_kernel    K x parts blocks (sample_body): warp 0 rolls
 //                         the sample out while the other warps stage the
 //                         obstacle points in shared memory, then every
-//                         (step, point) signed distance, then J~; when K
+//                         (step, point) signed distance that can matter
+//                         (far point sub-chunks skipped), then J~; when K
 //                         is small each sample's horizon is split over
 //                         several blocks (parts) to fill the GPU.
 //   mppi_update_kernel    ceil(K / chunk) blocks (update_body): weights and
@@ -19,6 +20,8 @@
 // The footprint constants are kernel parameters (compile-time edge count).
 // No K x T x N intermediate exists; scratch is per-sample J~ / weights,
 // per-block partial sums and per-step nominal data in the context arena.
+// The kernels live in mppi_kernels.cuh; this file instantiates them for
+// static clouds and mppi_predicted.cu for clouds with point velocities.
 #include "mppi_kernels.cuh"
 
 namespace exact {

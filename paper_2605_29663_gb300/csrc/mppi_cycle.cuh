@@ -2,13 +2,16 @@
 // block-level device bodies, shared by the single-scene kernels (mppi.cu)
 // and the batched persistent kernels (batched.cu):
 //   sample_body    one sample r: rollout, every (step, point) body-frame
-//                  signed distance, per-step minima, J~ (Sec. III-E, IV-C..E)
+//                  signed distance, per-step minima, J~ (Sec. III-E, IV-C..E);
+//                  point sub-chunks that cannot come within d_safe of the
+//                  footprint are skipped when no d_min output is wanted
 //   update_body    one chunk of samples: weights and weighted clipped noise
 //                  into a partial slot (Alg. 1 step 3)
 //   validate_body  one (step, point chunk) of the nominal: adds the partial
 //                  slots (U_upd), rolls the nominal out, d_min >= d_safe;
 //                  the scene's last block writes u*, the shifted or reset U
-//                  and the valid flag (Alg. 1 step 4)
+//                  and the valid flag (Alg. 1 step 4), and the nominal's
+//                  cost when asked (the J_m of Alg. 2)
 // Blocks never wait for each other: the last block of a phase is found with
 // an atomic ticket.  A footprint is reached through an evaluator object that
 // provides eval2 (two points -> two order keys) and dist (key -> signed
