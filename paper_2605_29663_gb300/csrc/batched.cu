@@ -30,24 +30,9 @@
 #include <new>
 #include <vector>
 
-#include "mppi_cycle.cuh"
+#include "batched_internal.cuh"
 
 namespace exact {
-
-constexpr int kFpSlots = 2 * EXACT_MAX_POLY_VERTICES + 2;   // float4 footprint slots
-constexpr size_t kHdrStride = 64;                            // bytes between scene headers
-
-struct SceneDev {
-    SceneView V;
-    int kind, nfp;
-    float3 bc;    // footprint bounding circle
-    float4 fpc[kFpSlots];
-};
-
-__device__ __forceinline__ void load_fp(float4 *dst, const SceneDev &D) {
-    const int nf = D.kind == EXACT_FP_POLYGON ? 2 * D.nfp + 1 : D.nfp;
-    for (int i = threadIdx.x; i < nf; i += blockDim.x) dst[i] = D.fpc[i];
-}
 
 __global__ void __launch_bounds__(512)
 batched_sample_kernel(const SceneDev *__restrict__ scenes, const int2 *__restrict__ items, int n_items,
@@ -102,19 +87,6 @@ MppiP to_device_params(const exact_mppi_params *p);
 
 using namespace exact;
 
-struct exact_batch {
-    int n = 0;
-    void *dev = nullptr;
-    SceneDev *d_scenes = nullptr;      // for steps
-    SceneDev *d_tune = nullptr;        // same, without the dmin outputs (autotuning)
-    int2 *d_items = nullptr, *d_upd = nullptr, *d_val = nullptr;
-    int n_items = 0, n_upd = 0, n_val = 0;
-    char *d_ctrl = nullptr;            // n headers (kHdrStride apart) + queue head
-    size_t ctrl_bytes = 0;
-    unsigned *d_queue = nullptr;
-    size_t smem = 0;
-    int threads = kBlock, pairs = 1, sms = 0, grid = 0;
-};
 
 static int batch_grid(exact_batch *b) {
     int per_sm = 0;
@@ -187,6 +159,10 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
     b->n_val = (int)val.size();
     b->smem = kFpSlots * sizeof(float4) + (size_t)max_stage * sizeof(float2);
     b->sms = current_sm_count();
+    b->uniform = true;
+    for (int s = 1; s < n_scenes && b->uniform; ++s)
+        b->uniform = memcmp(scenes[s].fp, scenes[0].fp, sizeof(exact_footprint)) == 0;
+    if (b->uniform) b->fp = *scenes[0].fp;
 
     for (int s = 0; s < n_scenes; ++s) {
         const exact_scene &S = scenes[s];
@@ -253,9 +229,13 @@ extern "C" void exact_batch_destroy(exact_batch *b) {
 
 static int launch_sample(exact_batch *b, const SceneDev *table, cudaStream_t st) {
     if (cudaMemsetAsync(b->d_ctrl, 0, b->ctrl_bytes, st) != cudaSuccess) return EXACT_ECUDA;
-    batched_sample_kernel<<<b->grid, b->threads, b->smem, st>>>(table, b->d_items, b->n_items, b->d_queue,
-                                                                 b->pairs);
-    return cuda_status(cudaGetLastError());
+    if (!b->uniform) {
+        batched_sample_kernel<<<b->grid, b->threads, b->smem, st>>>(table, b->d_items, b->n_items, b->d_queue,
+                                                                     b->pairs);
+        return cuda_status(cudaGetLastError());
+    }
+    return b->fp.kind == EXACT_FP_POLYGON && b->fp.n_pad > 16 ? launch_uniform_large(b, table, st, false)
+                                                               : launch_uniform_small(b, table, st, false);
 }
 
 extern "C" int mppi_step_batched(exact_batch *b, void *stream) {
@@ -264,8 +244,12 @@ extern "C" int mppi_step_batched(exact_batch *b, void *stream) {
     int rc = launch_sample(b, b->d_scenes, st);
     if (rc != EXACT_OK) return rc;
     batched_update_kernel<<<b->n_upd, kUpdBlock, 0, st>>>(b->d_scenes, b->d_upd);
-    batched_validate_kernel<<<b->n_val, kBlock, 0, st>>>(b->d_scenes, b->d_val);
-    return cuda_status(cudaGetLastError());
+    if (!b->uniform) {
+        batched_validate_kernel<<<b->n_val, kBlock, 0, st>>>(b->d_scenes, b->d_val);
+        return cuda_status(cudaGetLastError());
+    }
+    return b->fp.kind == EXACT_FP_POLYGON && b->fp.n_pad > 16 ? launch_uniform_large(b, b->d_scenes, st, true)
+                                                               : launch_uniform_small(b, b->d_scenes, st, true);
 }
 
 extern "C" int exact_batch_get_tiles(const exact_batch *b, int *threads, int *pairs_per_lane) {
@@ -282,6 +266,7 @@ extern "C" int exact_batch_set_tiles(exact_batch *b, int threads, int pairs_per_
     const int ot = b->threads, op = b->pairs;
     b->threads = threads;
     b->pairs = pairs_per_lane;
+    b->grid_c = 0;
     const int rc = batch_grid(b);
     if (rc != EXACT_OK) {
         b->threads = ot;

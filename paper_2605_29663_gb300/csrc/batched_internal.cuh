@@ -1,0 +1,51 @@
+// batched_internal.cuh -- what batched.cu (plan, generic kernels) and
+// batched_uniform.cuh (constant-footprint kernels) share: the device scene
+// table entry and the batch plan.
+#pragma once
+
+#include "mppi_cycle.cuh"
+
+namespace exact {
+
+constexpr int kFpSlots = 2 * EXACT_MAX_POLY_VERTICES + 2;   // float4 footprint slots
+constexpr size_t kHdrStride = 64;                            // bytes between scene headers
+
+struct SceneDev {
+    SceneView V;
+    int kind, nfp;
+    float3 bc;    // footprint bounding circle
+    float4 fpc[kFpSlots];
+};
+
+__device__ __forceinline__ void load_fp(float4 *dst, const SceneDev &D) {
+    const int nf = D.kind == EXACT_FP_POLYGON ? 2 * D.nfp + 1 : D.nfp;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) dst[i] = D.fpc[i];
+}
+
+}  // namespace exact
+
+struct exact_batch {
+    int n = 0;
+    void *dev = nullptr;
+    exact::SceneDev *d_scenes = nullptr;      // for steps
+    exact::SceneDev *d_tune = nullptr;        // same, without the dmin outputs (autotuning)
+    int2 *d_items = nullptr, *d_upd = nullptr, *d_val = nullptr;
+    int n_items = 0, n_upd = 0, n_val = 0;
+    char *d_ctrl = nullptr;            // n headers (kHdrStride apart) + queue head
+    size_t ctrl_bytes = 0;
+    unsigned *d_queue = nullptr;
+    size_t smem = 0;
+    int threads = exact::kBlock, pairs = 1, sms = 0, grid = 0;
+    bool uniform = false;              // every scene has the same footprint constants
+    exact_footprint fp;                // their copy (uniform batches)
+    int grid_c = 0;                    // persistent grid of the constant-footprint kernel (0 = not yet known)
+};
+
+namespace exact {
+// Sample (validate = false) or validation launch of a batch whose scenes
+// share one footprint, footprint constants as kernel parameters
+// (batched_uniform.cuh): rectangle covers and polygons of up to 16 edges,
+// and larger polygons.
+int launch_uniform_small(exact_batch *b, const SceneDev *table, cudaStream_t st, bool validate);
+int launch_uniform_large(exact_batch *b, const SceneDev *table, cudaStream_t st, bool validate);
+}  // namespace exact

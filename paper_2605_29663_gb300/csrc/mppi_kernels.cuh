@@ -1,14 +1,19 @@
 // mppi_kernels.cuh -- the three kernels of one single-scene control cycle
 // and their stream-ordered launch, templated on static / predicted
-// (time-indexed) obstacle points.  mppi.cu instantiates the static cycle and
-// mppi_predicted.cu the predicted one, so the two compile in parallel.
+// (time-indexed) obstacle points and on the sample kernel's minimum resident
+// blocks per SM (MINB).  MINB = 4 caps the sample kernel at 64 registers:
+// four blocks per SM, which pays when the grid spans several waves; with
+// few samples (one wave or less) the uncapped kernel (MINB = 0: no bound,
+// the compiler's own register choice) finishes sooner.  mppi.cu instantiates the static
+// uncapped cycle, mppi_dense.cu the static capped one and mppi_predicted.cu
+// the predicted (capped) one, so the three compile in parallel.
 #pragma once
 #include "mppi_cycle.cuh"
 
 namespace exact {
 
-template <class FPC, bool MOVING>
-__global__ void __launch_bounds__(kBlock)
+template <class FPC, bool MOVING, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
 mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev) {
     extern __shared__ float2 s_pts[];   // min(N, stage) staged points (float4 each when MOVING)
     __shared__ SampleSmem sm;
@@ -51,13 +56,13 @@ cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned b
 }
 
 // The three launches of one cycle for a scene whose scratch is carved.
-template <bool MOVING>
+template <bool MOVING, int MINB>
 int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t st) {
     const size_t smem = (size_t)min(V.N, stage_points_of<MOVING>()) * (MOVING ? sizeof(float4) : sizeof(float2));
     return with_footprint(fp, [&](auto fpc) -> int {
         using FPC = decltype(fpc);
         const ConstEval<FPC> ev{fpc};
-        mppi_sample_kernel<FPC, MOVING><<<V.P.K * V.parts, kBlock, smem, st>>>(V, ev);
+        mppi_sample_kernel<FPC, MOVING, MINB><<<V.P.K * V.parts, kBlock, smem, st>>>(V, ev);
         if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
         if (launch_dependent(mppi_update_kernel<MOVING>, V.upd_blocks, kUpdBlock, 0, st, V) != cudaSuccess)
             return EXACT_ECUDA;
@@ -68,8 +73,10 @@ int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t s
     });
 }
 
-// Static cycle (mppi.cu) and predicted cycle (mppi_predicted.cu).
+// Any cycle (mppi.cu: picks one of the three below), the static capped cycle
+// (mppi_dense.cu) and the predicted cycle (mppi_predicted.cu).
 int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st);
+int launch_cycle_dense(const SceneView &V, const exact_footprint *fp, cudaStream_t st);
 int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st);
 
 // mppi_step with optional point velocities (NULL: static cloud).

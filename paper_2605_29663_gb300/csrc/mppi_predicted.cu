@@ -11,7 +11,7 @@
 namespace exact {
 
 int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st) {
-    return launch_cycle_t<true>(V, fp, st);
+    return launch_cycle_t<true, 4>(V, fp, st);
 }
 
 }  // namespace exact

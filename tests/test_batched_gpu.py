@@ -157,3 +157,25 @@ def test_autotune_persists_the_tile_shape(ex, tmp_path):
     b2.set_tiles(64, 8)
     rep2 = b2.autotune(iters=1, cache=cache)
     assert rep2["cached"] and b2.tiles == b1.tiles
+
+
+@pytest.mark.parametrize("kind", ["polygon", "rects"])
+def test_uniform_footprint_batch_equals_single_scene_bitwise(ex, kind):
+    """Scenes that share one footprint run the constant-footprint kernels;
+    each still gives the single-scene bits."""
+    g = synth.rng(91)
+    scenes = []
+    for i in range(5):
+        model = [synth.DIFF, synth.ACKERMANN, synth.OMNI][i % 3]
+        s = synth.random_scene(g, model, 12, int(g.integers(300, 3000)), int(g.choice([64, 200])), int(g.integers(8, 30)))
+        if kind == "polygon":
+            s["kind"], s["fp"] = synth.POLYGON, synth.l_footprint()
+        else:
+            s["kind"], s["fp"] = synth.RECTS, synth.forklift_rects() * np.float32(0.4)
+        scenes.append(s)
+    got = _run_batched(ex, scenes)
+    ctx = ex.Context()
+    for i, s in enumerate(scenes):
+        ref = _run_single(ex, ctx, s)
+        for key in ("dmin", "costs", "weights", "U_upd", "U", "u_star"):
+            np.testing.assert_array_equal(got[i][key], ref[key], err_msg=f"scene {i} {key}")
