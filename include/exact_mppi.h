@@ -38,7 +38,8 @@ typedef enum {
     EXACT_ENOTSIMPLE = 2,   /* polygon is not simple (self-intersection, repeated vertex, zero area) */
     EXACT_ECAPACITY = 3,    /* size beyond a documented maximum */
     EXACT_ECUDA = 4,        /* a CUDA runtime call failed */
-    EXACT_ETIMEOUT = 5      /* a bounded device-side wait gave up */
+    EXACT_ETIMEOUT = 5      /* a bounded device-side wait gave up (reserved: no kernel of this
+                               library waits on another block; phases end with atomic tickets) */
 } exact_status;
 
 typedef enum { EXACT_FP_POLYGON = 0, EXACT_FP_RECTS = 1 } exact_fp_kind;
@@ -144,7 +145,11 @@ typedef struct {
  *   weights   device, K, or NULL: omega per sample
  *   valid     device, 1 int32, or NULL: 1 if the updated nominal passed
  *   U_upd     device, T x n_u, or NULL: the updated nominal before shift/reset
- *   dmin      device, K x T, or NULL: d_min of every scored rollout state
+ *   dmin      device, K x T, or NULL: d_min of every scored rollout state.
+ *             Without it the sample phase skips point sub-chunks that cannot
+ *             come within d_safe of the footprint at a step: every cost term
+ *             and the validation test are the same for any d >= d_safe, so
+ *             costs, weights and U are identical either way
  * Limits: 1 <= K <= 65536, 1 <= T <= 128, n_points >= 0, n_wp >= 1,
  * n_u must match the model.  Scratch comes from ctx (grown on demand). */
 int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint8_t *mask,
