@@ -240,7 +240,7 @@ def mppi_extra(torch, ex, dev, cpu: bool = True):
              if k in ("q0", "cloud", "waypoints", "U", "eps") and v is not None}
         mask = torch.from_numpy(s["mask"]).to(dev) if s["mask"] is not None else None
         U = t["U"].clone()
-        ctx.reserve(0, p["K"], p["T"])
+        ctx.reserve(0, p["K"], p["T"], s["cloud"].shape[0])
         outs = {}
 
         def step():
@@ -272,7 +272,7 @@ def predicted_extra(torch, ex, dev, cpu: bool = True):
     t = {k: torch.from_numpy(s[k]).to(dev) for k in ("q0", "cloud", "vel", "waypoints", "U", "eps")}
     mask = torch.from_numpy(s["mask"]).to(dev) if s["mask"] is not None else None
     ctx = ex.Context()
-    ctx.reserve(0, p["K"], p["T"])
+    ctx.reserve(0, p["K"], p["T"], s["cloud"].shape[0])
     out = {}
     res = {}
     for name, vel in (("predicted", t["vel"]), ("static", None)):
@@ -484,7 +484,8 @@ def batched_extra(torch, ex, dev, steps=3, tune=True):
     torch.cuda.synchronize()
     ms_b = e0.elapsed_time(e1) / steps
     ctx = ex.Context()
-    ctx.reserve(0, max(s["params"]["K"] for s in scenes), max(s["params"]["T"] for s in scenes))
+    ctx.reserve(0, max(s["params"]["K"] for s in scenes), max(s["params"]["T"] for s in scenes),
+                max(s["cloud"].shape[0] for s in scenes))
     outs = [dict() for _ in devs]
 
     def singles():
@@ -531,7 +532,7 @@ def run_mppi_workload(args):
         vel = torch.from_numpy(s["vel"]).to(dev) if args.workload == "predicted" else None
         mask = torch.from_numpy(s["mask"]).to(dev) if s["mask"] is not None else None
         ctx = ex.Context()
-        ctx.reserve(0, p["K"], p["T"])
+        ctx.reserve(0, p["K"], p["T"], s["cloud"].shape[0])
         outs = {}
 
         def step():

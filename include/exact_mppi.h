@@ -89,6 +89,12 @@ void exact_ctx_destroy(exact_ctx *ctx);
 /* Make sure scratch for sdf batches of up to max_poses poses and MPPI steps
  * of up to max_K samples and max_T steps exists (synchronous). */
 int exact_ctx_reserve(exact_ctx *ctx, int max_poses, int max_K, int max_T);
+/* The same, also for clouds of up to max_points points: an MPPI step without
+ * a d_min output keeps a spatially ordered copy of clouds of 1,024 points or
+ * more in the context (it makes the pruning of far points effective whatever
+ * the input order), so a step with a larger cloud than any before may
+ * allocate -- reserve ahead of stream capture. */
+int exact_ctx_reserve_cloud(exact_ctx *ctx, int max_poses, int max_K, int max_T, int max_points);
 /* Device-side error word (an exact_status); synchronises the device, then
  * returns and clears it. */
 int exact_ctx_get_error(exact_ctx *ctx);

@@ -26,6 +26,7 @@ NU = {DIFF: 2, ACKERMANN: 2, OMNI: 3, SPIN: 1, PARALLEL: 1}
 # every symbol declared in include/exact_mppi.h
 EXPORTS = ["exact_status_string", "exact_footprint_create", "exact_footprint_destroy",
            "exact_footprint_info", "exact_ctx_create", "exact_ctx_destroy", "exact_ctx_reserve",
+           "exact_ctx_reserve_cloud",
            "exact_ctx_get_error", "exact_sdf_batch", "mppi_step", "mppi_step_predicted", "exact_batch_create",
            "exact_batch_destroy",
            "mppi_step_batched", "exact_batch_autotune", "exact_batch_get_tiles", "exact_batch_set_tiles",
@@ -70,6 +71,8 @@ def load() -> ctypes.CDLL:
         lib.exact_ctx_destroy.argtypes = [P]
         lib.exact_ctx_reserve.restype = I
         lib.exact_ctx_reserve.argtypes = [P, I, I, I]
+        lib.exact_ctx_reserve_cloud.restype = I
+        lib.exact_ctx_reserve_cloud.argtypes = [P, I, I, I, I]
         lib.exact_ctx_get_error.restype = I
         lib.exact_ctx_get_error.argtypes = [P]
         lib.exact_sdf_batch.restype = I
@@ -219,8 +222,12 @@ class Context:
     def handle(self):
         return self._h
 
-    def reserve(self, max_poses: int = 0, max_K: int = 0, max_T: int = 0):
-        _check(load().exact_ctx_reserve(self._h, max_poses, max_K, max_T), "exact_ctx_reserve")
+    def reserve(self, max_poses: int = 0, max_K: int = 0, max_T: int = 0, max_points: int = 0):
+        """Allocate scratch ahead of time (before a CUDA graph capture): SDF
+        batches of max_poses poses, MPPI steps of max_K x max_T, clouds of
+        max_points points (their spatially ordered copy)."""
+        _check(load().exact_ctx_reserve_cloud(self._h, max_poses, max_K, max_T, max_points),
+               "exact_ctx_reserve_cloud")
 
     def get_error(self) -> int:
         return load().exact_ctx_get_error(self._h)

@@ -61,6 +61,14 @@ batched_sample_kernel(const SceneDev *__restrict__ scenes, const int2 *__restric
     }
 }
 
+// Spatially ordered cloud copies of the scenes that prune (one block each).
+__global__ void __launch_bounds__(kSortThreads)
+batched_sort_kernel(const SceneDev *__restrict__ scenes, const int *__restrict__ list) {
+    __shared__ SortSmem sm;
+    const SceneDev &D = scenes[list[blockIdx.x]];
+    sort_cloud_block<false>(D.src_pts, nullptr, D.src_mask, D.V.N, const_cast<float2 *>(D.V.pts), nullptr, sm);
+}
+
 __global__ void __launch_bounds__(kUpdBlock)
 batched_update_kernel(const SceneDev *__restrict__ scenes, const int2 *__restrict__ table) {
     __shared__ UpdateSmem sm;
@@ -115,8 +123,13 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         if (S.n_points > 0 && (!S.cloud || ((uintptr_t)S.cloud & 7u) != 0)) return EXACT_EINVAL;
         scratch_off[s] = scratch_total;
         scratch_total += align_up(scene_scratch_bytes(S.params.K, S.params.T, 1), 256);
+        // scenes that prune (no d_min output, large cloud) get a spatially ordered cloud copy
+        if (!S.dmin && S.n_points >= kPruneMin) scratch_total += align_up((size_t)S.n_points * sizeof(float2), 256);
         max_stage = std::max(max_stage, std::min(S.n_points, kStage));
     }
+    std::vector<int> sort_list;
+    for (int s = 0; s < n_scenes; ++s)
+        if (!scenes[s].dmin && scenes[s].n_points >= kPruneMin) sort_list.push_back(s);
     const size_t table_bytes = align_up(sizeof(SceneDev) * n_scenes, 256);
     // items and block tables
     std::vector<int> order(n_scenes);
@@ -138,7 +151,9 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
     const size_t upd_bytes = align_up(upd.size() * sizeof(int2), 256);
     const size_t val_bytes = align_up(val.size() * sizeof(int2), 256);
     const size_t ctrl_bytes = align_up(kHdrStride * n_scenes + sizeof(unsigned), 256);
-    const size_t total = 2 * table_bytes + items_bytes + upd_bytes + val_bytes + ctrl_bytes + scratch_total;
+    const size_t sort_bytes = align_up(sort_list.size() * sizeof(int) + 1, 256);
+    const size_t total =
+        2 * table_bytes + items_bytes + upd_bytes + val_bytes + ctrl_bytes + sort_bytes + scratch_total;
 
     exact_batch *b = new (std::nothrow) exact_batch();
     if (!b) return EXACT_EINVAL;
@@ -150,6 +165,8 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
     b->d_upd = reinterpret_cast<int2 *>(p); p += upd_bytes;
     b->d_val = reinterpret_cast<int2 *>(p); p += val_bytes;
     b->d_ctrl = p; p += ctrl_bytes;
+    b->d_sort = reinterpret_cast<int *>(p); p += sort_bytes;
+    b->n_sort = (int)sort_list.size();
     char *scratch = p;
     b->ctrl_bytes = ctrl_bytes;
     b->d_queue = reinterpret_cast<unsigned *>(b->d_ctrl + kHdrStride * n_scenes);
@@ -182,6 +199,13 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         V.dmin = S.dmin; V.valid = S.valid; V.nom_cost = S.nom_cost;
         V.hdr = reinterpret_cast<ArenaHeader *>(b->d_ctrl + kHdrStride * s);
         carve_scene(V, scratch + scratch_off[s], S.params.K, S.params.T, 1);
+        D.src_pts = V.pts;
+        D.src_mask = V.mask;
+        if (!S.dmin && S.n_points >= kPruneMin) {   // the sort kernel fills the copy before each step
+            V.pts = reinterpret_cast<const float2 *>(scratch + scratch_off[s] +
+                                                     align_up(scene_scratch_bytes(S.params.K, S.params.T, 1), 256));
+            V.mask = nullptr;
+        }
         V.upd_chunk = upd_chunk_for(S.params.K, S.params.T, S.params.n_u);
         V.upd_blocks = upd_blocks_for(S.params.K, S.params.T, S.params.n_u);
         V.val_chunks = val_chunks_for(S.n_points);
@@ -207,6 +231,8 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_upd, upd.data(), upd.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_val, val.data(), val.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (b->n_sort && cudaMemcpy(b->d_sort, sort_list.data(), sort_list.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+                          cudaSuccess) ||
         cudaMemset(b->d_ctrl, 0, ctrl_bytes) != cudaSuccess ||
         (scratch_total && cudaMemset(scratch, 0, scratch_total) != cudaSuccess))
         rc = EXACT_ECUDA;
@@ -229,6 +255,10 @@ extern "C" void exact_batch_destroy(exact_batch *b) {
 
 static int launch_sample(exact_batch *b, const SceneDev *table, cudaStream_t st) {
     if (cudaMemsetAsync(b->d_ctrl, 0, b->ctrl_bytes, st) != cudaSuccess) return EXACT_ECUDA;
+    if (b->n_sort > 0) {
+        batched_sort_kernel<<<b->n_sort, kSortThreads, 0, st>>>(table, b->d_sort);
+        if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
+    }
     if (!b->uniform) {
         batched_sample_kernel<<<b->grid, b->threads, b->smem, st>>>(table, b->d_items, b->n_items, b->d_queue,
                                                                      b->pairs);

@@ -12,6 +12,8 @@ constexpr size_t kHdrStride = 64;                            // bytes between sc
 
 struct SceneDev {
     SceneView V;
+    const float2 *src_pts;      // the caller's cloud (V.pts may be its spatially ordered copy)
+    const uint8_t *src_mask;
     int kind, nfp;
     float3 bc;    // footprint bounding circle
     float4 fpc[kFpSlots];
@@ -34,6 +36,8 @@ struct exact_batch {
     char *d_ctrl = nullptr;            // n headers (kHdrStride apart) + queue head
     size_t ctrl_bytes = 0;
     unsigned *d_queue = nullptr;
+    int *d_sort = nullptr;             // scenes whose cloud gets a spatially ordered copy
+    int n_sort = 0;
     size_t smem = 0;
     int threads = exact::kBlock, pairs = 1, sms = 0, grid = 0;
     bool uniform = false;              // every scene has the same footprint constants

@@ -59,9 +59,14 @@ MppiP to_device_params(const exact_mppi_params *p) {
 using namespace exact;
 
 extern "C" int exact_ctx_reserve(exact_ctx *ctx, int max_poses, int max_K, int max_T) {
-    if (!ctx || max_poses < 0 || max_K < 0 || max_T < 0) return EXACT_EINVAL;
+    return exact_ctx_reserve_cloud(ctx, max_poses, max_K, max_T, 0);
+}
+
+extern "C" int exact_ctx_reserve_cloud(exact_ctx *ctx, int max_poses, int max_K, int max_T, int max_points) {
+    if (!ctx || max_poses < 0 || max_K < 0 || max_T < 0 || max_points < 0) return EXACT_EINVAL;
     size_t need = sdf_scratch_bytes(max_poses);
-    const size_t m = kArenaHeader + scene_scratch_bytes(max_K, max_T, parts_of(ctx, max_K, max_T));
+    const size_t m = kArenaHeader + scene_scratch_bytes(max_K, max_T, parts_of(ctx, max_K, max_T)) +
+                     (max_points >= kPruneMin ? cloud_copy_bytes(max_points, true) : 0);
     if (m > need) need = m;
     return ensure_scratch(ctx, need);
 }
@@ -79,7 +84,11 @@ int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const
     if (rc != EXACT_OK) return rc;
     const MppiP P = to_device_params(params);
     const int parts = parts_of(ctx, P.K, P.T);
-    rc = ensure_scratch(ctx, kArenaHeader + scene_scratch_bytes(P.K, P.T, parts));
+    // without a d_min output the sample phase prunes; it pays when the cloud
+    // is in spatial order, so large clouds get a spatially ordered copy
+    const bool sort = !dmin && n_points >= kPruneMin;
+    const size_t scene_bytes = kArenaHeader + scene_scratch_bytes(P.K, P.T, parts);
+    rc = ensure_scratch(ctx, scene_bytes + (sort ? cloud_copy_bytes(n_points, velocity != nullptr) : 0));
     if (rc != EXACT_OK) return rc;
     SceneView V;
     V.P = P;
@@ -107,6 +116,20 @@ int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const
         if (cudaMemsetAsync(V.tk, 0, (size_t)P.K * sizeof(unsigned), st) != cudaSuccess) return EXACT_ECUDA;
     }
     ctx->mppi_layout = layout;
+    if (sort) {
+        float2 *copy = reinterpret_cast<float2 *>(static_cast<char *>(ctx->scratch) + scene_bytes);
+        float2 *vcopy = velocity ? reinterpret_cast<float2 *>(reinterpret_cast<char *>(copy) +
+                                                             align_up((size_t)n_points * sizeof(float2), 256))
+                                 : nullptr;
+        if (velocity)
+            cloud_sort_kernel<true><<<1, kSortThreads, 0, st>>>(V.pts, V.vel, mask, n_points, copy, vcopy);
+        else
+            cloud_sort_kernel<false><<<1, kSortThreads, 0, st>>>(V.pts, nullptr, mask, n_points, copy, nullptr);
+        if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
+        V.pts = copy;
+        V.vel = vcopy;
+        V.mask = nullptr;
+    }
     return launch_cycle(V, fp, st);
 }
 

@@ -262,6 +262,94 @@ __device__ __forceinline__ void chunk_circles(const float2 *pts, int n, float4 *
     }
 }
 
+// ---------------------------------------------------------------- cloud order
+// Pruning pays only when 64 consecutive points lie close together.  Scans
+// deliver clouds in that order; for any other order one block rewrites the
+// cloud in Morton order of a 64 x 64 grid over its bounding box (a counting
+// sort: histogram, prefix sum, scatter).  Masked and non-finite points go
+// last, as NaN, so the copy needs no mask.  The order inside a grid cell
+// follows the scatter's atomics; nothing computed from the cloud depends on
+// it (minima over points are exact whatever the order).
+constexpr int kSortCells = 64 * 64;
+constexpr int kSortThreads = 1024;
+struct SortSmem {
+    int cnt[kSortCells + 1];
+    float red[4][kSortThreads / 32];
+    int part[kSortThreads / 32];
+};
+
+__device__ __forceinline__ unsigned morton6(unsigned x, unsigned y) {
+    unsigned r = 0u;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) r |= (((x >> b) & 1u) << (2 * b)) | (((y >> b) & 1u) << (2 * b + 1));
+    return r;
+}
+
+template <bool MOVING>
+__device__ __forceinline__ void sort_cloud_block(const float2 *__restrict__ pts, const float2 *__restrict__ vel,
+                                                 const uint8_t *__restrict__ mask, int N, float2 *__restrict__ opts,
+                                                 float2 *__restrict__ ovel, SortSmem &sm) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    auto valid = [&](int i, float2 &p) {
+        p = pts[i];
+        return (!mask || mask[i]) && isfinite(p.x) && isfinite(p.y);
+    };
+    float lx = finf(), ly = finf(), hx = -finf(), hy = -finf();
+    for (int i = tid; i < N; i += nt) {
+        float2 p;
+        if (valid(i, p)) { lx = fminf(lx, p.x); hx = fmaxf(hx, p.x); ly = fminf(ly, p.y); hy = fmaxf(hy, p.y); }
+    }
+    lx = warp_min_f(lx); ly = warp_min_f(ly); hx = -warp_min_f(-hx); hy = -warp_min_f(-hy);
+    if (lane == 0) { sm.red[0][warp] = lx; sm.red[1][warp] = ly; sm.red[2][warp] = hx; sm.red[3][warp] = hy; }
+    for (int c = tid; c <= kSortCells; c += nt) sm.cnt[c] = 0;
+    __syncthreads();
+    lx = ly = finf(); hx = hy = -finf();
+    for (int w = 0; w < nw; ++w) {
+        lx = fminf(lx, sm.red[0][w]); ly = fminf(ly, sm.red[1][w]);
+        hx = fmaxf(hx, sm.red[2][w]); hy = fmaxf(hy, sm.red[3][w]);
+    }
+    const float sx = 64.f / fmaxf(hx - lx, 1e-6f), sy = 64.f / fmaxf(hy - ly, 1e-6f);
+    auto cell = [&](int i, float2 &p) -> int {
+        if (!valid(i, p)) return kSortCells;
+        const int qx = min(63, max(0, (int)((p.x - lx) * sx))), qy = min(63, max(0, (int)((p.y - ly) * sy)));
+        return (int)morton6((unsigned)qx, (unsigned)qy);
+    };
+    for (int i = tid; i < N; i += nt) {
+        float2 p;
+        atomicAdd(&sm.cnt[cell(i, p)], 1);
+    }
+    __syncthreads();
+    // exclusive prefix over the kSortCells + 1 counts: contiguous segments per thread
+    const int per = (kSortCells + 1 + nt - 1) / nt, c0 = tid * per, c1 = min(kSortCells + 1, c0 + per);
+    int s = 0;
+    for (int c = c0; c < c1; ++c) s += sm.cnt[c];
+    int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) sm.part[warp] = inc;
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < warp; ++w) base += sm.part[w];
+    int run = base + inc - s;
+    for (int c = c0; c < c1; ++c) {
+        const int v = sm.cnt[c];
+        sm.cnt[c] = run;
+        run += v;
+    }
+    __syncthreads();
+    const float qnan = __int_as_float(0x7fffffff);
+    for (int i = tid; i < N; i += nt) {
+        float2 p;
+        const int c = cell(i, p);
+        const int pos = atomicAdd(&sm.cnt[c], 1);
+        opts[pos] = c < kSortCells ? p : make_float2(qnan, qnan);
+        if (MOVING) ovel[pos] = c < kSortCells ? vel[i] : make_float2(0.f, 0.f);
+    }
+}
+
 // ---------------------------------------------------------------- sample phase
 // Per-step minimum of the body-frame key over n staged points for the steps
 // [h0, h0 + nh) whose poses are in shared memory.  Masked points were staged

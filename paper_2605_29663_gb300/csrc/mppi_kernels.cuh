@@ -38,6 +38,20 @@ __global__ void __launch_bounds__(kBlock) mppi_validate_kernel(const SceneView V
     validate_body<MOVING>(V, ev, blockIdx.x / V.val_chunks, blockIdx.x % V.val_chunks, sm);
 }
 
+// One block rewrites the cloud in spatial order (see sort_cloud_block).
+template <bool MOVING>
+__global__ void __launch_bounds__(kSortThreads)
+cloud_sort_kernel(const float2 *pts, const float2 *vel, const uint8_t *mask, int N, float2 *opts, float2 *ovel) {
+    __shared__ SortSmem sm;
+    sort_cloud_block<MOVING>(pts, vel, mask, N, opts, ovel, sm);
+}
+
+// Bytes of the spatially ordered cloud copy (points, and velocities when
+// predicted) that follows a scene's scratch in the context arena.
+inline size_t cloud_copy_bytes(int N, bool moving) {
+    return align_up((size_t)N * sizeof(float2), 256) * (moving ? 2 : 1);
+}
+
 // Launch with the programmatic-serialization attribute (see grid_dep_wait).
 template <typename... KArgs, typename... Args>
 cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,

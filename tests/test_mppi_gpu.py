@@ -295,3 +295,21 @@ def test_largest_sample_count(ex, ctx):
     if o["n_near"]:
         pytest.skip("threshold-adjacent d_min in this seed")
     compare(s, run_gpu(ex, ctx, s), o)
+
+
+@pytest.mark.parametrize("masked", [False, True])
+def test_cloud_order_changes_nothing(ex, ctx, masked):
+    """Without a d_min output large clouds are put in spatial order before the
+    sample phase; the costs depend only on the set of points, so a shuffled
+    cloud gives the same bits as the original, and both the bits of the run
+    that outputs d_min (no reordering, no pruning)."""
+    s = _coherent_scene(5, 384, 20, 3000, mask_tail=40 if masked else 0)
+    perm = synth.rng(6).permutation(s["cloud"].shape[0])
+    t = dict(s, cloud=np.ascontiguousarray(s["cloud"][perm]),
+             mask=None if s["mask"] is None else np.ascontiguousarray(s["mask"][perm]))
+    a = run_gpu(ex, ctx, s, dmin=False)
+    b = run_gpu(ex, ctx, t, dmin=False)
+    c = run_gpu(ex, ctx, t, dmin=True)
+    for k in ("costs", "weights", "U_upd", "U", "u_star"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+        np.testing.assert_array_equal(b[k], c[k], err_msg=k)
