@@ -260,6 +260,11 @@ static int launch_sample(exact_batch *b, const SceneDev *table, cudaStream_t st)
         if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
     }
     if (!b->uniform) {
+        // behind the cloud-ordering kernel the persistent blocks start early
+        // (rollouts first; sample_body waits before it reads a cloud)
+        if (b->n_sort > 0)
+            return cuda_status(launch_dependent(batched_sample_kernel, (unsigned)b->grid, (unsigned)b->threads, b->smem,
+                                                st, table, (const int2 *)b->d_items, b->n_items, b->d_queue, b->pairs));
         batched_sample_kernel<<<b->grid, b->threads, b->smem, st>>>(table, b->d_items, b->n_items, b->d_queue,
                                                                      b->pairs);
         return cuda_status(cudaGetLastError());

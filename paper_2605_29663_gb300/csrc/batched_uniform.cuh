@@ -52,6 +52,10 @@ int launch_uniform_sample_t(exact_batch *b, const SceneDev *table, cudaStream_t 
             return EXACT_ECUDA;
         b->grid_c = b->sms * per_sm;
     }
+    if (b->n_sort > 0)   // behind the cloud-ordering kernel: start early (see batched.cu)
+        return cuda_status(launch_dependent(k, (unsigned)b->grid_c, (unsigned)b->threads, b->smem, st, table,
+                                            (const int2 *)b->d_items, b->n_items, b->d_queue, b->pairs,
+                                            ConstEval<FPC>{fpc}));
     k<<<b->grid_c, b->threads, b->smem, st>>>(table, b->d_items, b->n_items, b->d_queue, b->pairs,
                                               ConstEval<FPC>{fpc});
     return cuda_status(cudaGetLastError());

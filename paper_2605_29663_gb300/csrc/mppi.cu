@@ -130,7 +130,7 @@ int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const
         V.vel = vcopy;
         V.mask = nullptr;
     }
-    return launch_cycle(V, fp, st);
+    return launch_cycle(V, fp, st, sort);
 }
 
 // Clouds with point velocities go to mppi_predicted.cu.  Static clouds go to
@@ -138,13 +138,14 @@ int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const
 // four blocks per SM and the footprint is small (a rectangle cover or at most
 // 16 edges: larger polygons need more registers than the cap leaves), else
 // to the uncapped ones here.
-int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st) {
-    if (V.vel) return launch_cycle_moving(V, fp, st);
+int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl) {
+    if (V.vel) return launch_cycle_moving(V, fp, st, pdl);
     static thread_local int sms = 0;
     if (sms <= 0) sms = current_sm_count();
     const bool small_fp = fp->kind == EXACT_FP_RECTS || fp->n_pad <= 16;
-    if (small_fp && (long long)V.P.K * V.parts > 4LL * (sms > 0 ? sms : 148)) return launch_cycle_dense(V, fp, st);
-    return launch_cycle_t<false, 0>(V, fp, st);
+    if (small_fp && (long long)V.P.K * V.parts > 4LL * (sms > 0 ? sms : 148))
+        return launch_cycle_dense(V, fp, st, pdl);
+    return launch_cycle_t<false, 0>(V, fp, st, pdl);
 }
 
 }  // namespace exact

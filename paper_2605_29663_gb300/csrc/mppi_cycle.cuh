@@ -80,6 +80,24 @@ inline int upd_blocks_for(int K, int T, int nu) {
 // completed and its writes are visible (a no-op without the attribute).
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch with the programmatic-serialization attribute (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                             cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 inline int val_chunks_for(int N) {
     const int np = (N + 1) / 2;
     return np > kValChunkPairs ? (np + kValChunkPairs - 1) / kValChunkPairs : 1;
@@ -290,6 +308,7 @@ __device__ __forceinline__ void sort_cloud_block(const float2 *__restrict__ pts,
                                                  const uint8_t *__restrict__ mask, int N, float2 *__restrict__ opts,
                                                  float2 *__restrict__ ovel, SortSmem &sm) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    grid_dep_release();   // the sample kernel may start its rollouts meanwhile
     auto valid = [&](int i, float2 &p) {
         p = pts[i];
         return (!mask || mask[i]) && isfinite(p.x) && isfinite(p.y);
@@ -595,9 +614,10 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
             }
         }
         if (lane == 0) sm.term = P.w_term * guidance_dist(R.qTx, R.qTy, V.wp, V.W);
-
-    } else if (!staged) {
-        stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, 0, n0, threadIdx.x - 32, blockDim.x - 32);
+        grid_dep_wait();   // launched early behind a cloud-ordering kernel: the cloud is ready now
+    } else {
+        grid_dep_wait();
+        if (!staged) stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, 0, n0, threadIdx.x - 32, blockDim.x - 32);
     }
     __syncthreads();
     const bool prune = !V.dmin && N >= kPruneMin;

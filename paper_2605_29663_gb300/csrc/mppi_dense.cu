@@ -6,8 +6,8 @@
 
 namespace exact {
 
-int launch_cycle_dense(const SceneView &V, const exact_footprint *fp, cudaStream_t st) {
-    return launch_cycle_t<false, 4>(V, fp, st);
+int launch_cycle_dense(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl) {
+    return launch_cycle_t<false, 4>(V, fp, st, pdl);
 }
 
 }  // namespace exact

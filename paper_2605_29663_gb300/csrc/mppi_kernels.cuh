@@ -52,32 +52,24 @@ inline size_t cloud_copy_bytes(int N, bool moving) {
     return align_up((size_t)N * sizeof(float2), 256) * (moving ? 2 : 1);
 }
 
-// Launch with the programmatic-serialization attribute (see grid_dep_wait).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
-                             cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
 
 // The three launches of one cycle for a scene whose scratch is carved.
+// pdl: the sample kernel follows a cloud-ordering kernel and may start early
+// (its rollouts do not read the cloud; sample_body waits before staging).
 template <bool MOVING, int MINB>
-int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t st) {
+int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl = false) {
     const size_t smem = (size_t)min(V.N, stage_points_of<MOVING>()) * (MOVING ? sizeof(float4) : sizeof(float2));
     return with_footprint(fp, [&](auto fpc) -> int {
         using FPC = decltype(fpc);
         const ConstEval<FPC> ev{fpc};
-        mppi_sample_kernel<FPC, MOVING, MINB><<<V.P.K * V.parts, kBlock, smem, st>>>(V, ev);
-        if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
+        if (pdl) {
+            if (launch_dependent(mppi_sample_kernel<FPC, MOVING, MINB>, V.P.K * V.parts, kBlock, smem, st, V, ev) !=
+                cudaSuccess)
+                return EXACT_ECUDA;
+        } else {
+            mppi_sample_kernel<FPC, MOVING, MINB><<<V.P.K * V.parts, kBlock, smem, st>>>(V, ev);
+            if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
+        }
         if (launch_dependent(mppi_update_kernel<MOVING>, V.upd_blocks, kUpdBlock, 0, st, V) != cudaSuccess)
             return EXACT_ECUDA;
         if (launch_dependent(mppi_validate_kernel<FPC, MOVING>, V.P.T * V.val_chunks, kBlock, 0, st, V, ev) !=
@@ -89,9 +81,9 @@ int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t s
 
 // Any cycle (mppi.cu: picks one of the three below), the static capped cycle
 // (mppi_dense.cu) and the predicted cycle (mppi_predicted.cu).
-int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st);
-int launch_cycle_dense(const SceneView &V, const exact_footprint *fp, cudaStream_t st);
-int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st);
+int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl = false);
+int launch_cycle_dense(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl);
+int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl);
 
 // mppi_step with optional point velocities (NULL: static cloud).
 int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const float *velocity,

@@ -10,8 +10,8 @@
 
 namespace exact {
 
-int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st) {
-    return launch_cycle_t<true, 4>(V, fp, st);
+int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl) {
+    return launch_cycle_t<true, 4>(V, fp, st, pdl);
 }
 
 }  // namespace exact
