@@ -56,7 +56,7 @@ batched_sample_kernel(const SceneDev *__restrict__ scenes, const int2 *__restric
             fp_scene = it.x;
         }
         const SmemEval ev{s_fp, D.kind, D.nfp, D.bc};
-        sample_body(D.V, ev, it.y, 0, sm, s_pts, it.x == pts_scene, pairs_per_lane);
+        sample_body(D.V, ev, it.y, 0, sm, s_pts, it.x == pts_scene, pairs_per_lane, D.circ);
         pts_scene = D.V.N <= kStage ? it.x : -1;
     }
 }
@@ -67,6 +67,8 @@ batched_sort_kernel(const SceneDev *__restrict__ scenes, const int *__restrict__
     __shared__ SortSmem sm;
     const SceneDev &D = scenes[list[blockIdx.x]];
     sort_cloud_block<false>(D.src_pts, nullptr, D.src_mask, D.V.N, const_cast<float2 *>(D.V.pts), nullptr, sm);
+    __syncthreads();
+    cloud_circles<false>(D.V.pts, nullptr, D.V.N, const_cast<float4 *>(D.circ));
 }
 
 __global__ void __launch_bounds__(kUpdBlock)
@@ -85,7 +87,7 @@ batched_validate_kernel(const SceneDev *__restrict__ scenes, const int2 *__restr
     load_fp(s_fp, D);
     __syncthreads();
     const SmemEval ev{s_fp, D.kind, D.nfp, D.bc};
-    validate_body(D.V, ev, t.y / D.V.val_chunks, t.y % D.V.val_chunks, sm);
+    validate_body(D.V, ev, t.y / D.V.val_chunks, t.y % D.V.val_chunks, sm, D.circ);
 }
 
 int check_params(const exact_mppi_params *p);
@@ -124,7 +126,9 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         scratch_off[s] = scratch_total;
         scratch_total += align_up(scene_scratch_bytes(S.params.K, S.params.T, 1), 256);
         // scenes that prune (no d_min output, large cloud) get a spatially ordered cloud copy
-        if (!S.dmin && S.n_points >= kPruneMin) scratch_total += align_up((size_t)S.n_points * sizeof(float2), 256);
+        if (!S.dmin && S.n_points >= kPruneMin)
+            scratch_total += align_up((size_t)S.n_points * sizeof(float2), 256) +
+                             align_up((size_t)((S.n_points + kSub - 1) / kSub) * sizeof(float4), 256);
         max_stage = std::max(max_stage, std::min(S.n_points, kStage));
     }
     std::vector<int> sort_list;
@@ -202,8 +206,9 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         D.src_pts = V.pts;
         D.src_mask = V.mask;
         if (!S.dmin && S.n_points >= kPruneMin) {   // the sort kernel fills the copy before each step
-            V.pts = reinterpret_cast<const float2 *>(scratch + scratch_off[s] +
-                                                     align_up(scene_scratch_bytes(S.params.K, S.params.T, 1), 256));
+            char *q = scratch + scratch_off[s] + align_up(scene_scratch_bytes(S.params.K, S.params.T, 1), 256);
+            V.pts = reinterpret_cast<const float2 *>(q);
+            D.circ = reinterpret_cast<const float4 *>(q + align_up((size_t)S.n_points * sizeof(float2), 256));
             V.mask = nullptr;
         }
         V.upd_chunk = upd_chunk_for(S.params.K, S.params.T, S.params.n_u);

@@ -14,6 +14,7 @@ struct SceneDev {
     SceneView V;
     const float2 *src_pts;      // the caller's cloud (V.pts may be its spatially ordered copy)
     const uint8_t *src_mask;
+    const float4 *circ;         // sub-chunk circles of the ordered copy, or NULL
     int kind, nfp;
     float3 bc;    // footprint bounding circle
     float4 fpc[kFpSlots];

@@ -27,7 +27,7 @@ batched_sample_kernel_c(const SceneDev *__restrict__ scenes, const int2 *__restr
         if (item >= n_items) break;
         const int2 it = items[item];
         const SceneDev &D = scenes[it.x];
-        sample_body(D.V, ev, it.y, 0, sm, s_pts, it.x == pts_scene, pairs_per_lane);
+        sample_body(D.V, ev, it.y, 0, sm, s_pts, it.x == pts_scene, pairs_per_lane, D.circ);
         pts_scene = D.V.N <= kStage ? it.x : -1;
     }
 }
@@ -39,7 +39,7 @@ batched_validate_kernel_c(const SceneDev *__restrict__ scenes, const int2 *__res
     __shared__ ValidateSmem sm;
     const int2 t = table[blockIdx.x];
     const SceneDev &D = scenes[t.x];
-    validate_body(D.V, ev, t.y / D.V.val_chunks, t.y % D.V.val_chunks, sm);
+    validate_body(D.V, ev, t.y / D.V.val_chunks, t.y % D.V.val_chunks, sm, D.circ);
 }
 
 template <class FPC>

@@ -116,36 +116,39 @@ int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const
         if (cudaMemsetAsync(V.tk, 0, (size_t)P.K * sizeof(unsigned), st) != cudaSuccess) return EXACT_ECUDA;
     }
     ctx->mppi_layout = layout;
+    const float4 *cc = nullptr;
     if (sort) {
-        float2 *copy = reinterpret_cast<float2 *>(static_cast<char *>(ctx->scratch) + scene_bytes);
-        float2 *vcopy = velocity ? reinterpret_cast<float2 *>(reinterpret_cast<char *>(copy) +
-                                                             align_up((size_t)n_points * sizeof(float2), 256))
-                                 : nullptr;
+        char *q = static_cast<char *>(ctx->scratch) + scene_bytes;
+        const size_t pbytes = align_up((size_t)n_points * sizeof(float2), 256);
+        float2 *copy = reinterpret_cast<float2 *>(q);
+        float2 *vcopy = velocity ? reinterpret_cast<float2 *>(q + pbytes) : nullptr;
+        float4 *circ = reinterpret_cast<float4 *>(q + pbytes * (velocity ? 2 : 1));
         if (velocity)
-            cloud_sort_kernel<true><<<1, kSortThreads, 0, st>>>(V.pts, V.vel, mask, n_points, copy, vcopy);
+            cloud_sort_kernel<true><<<1, kSortThreads, 0, st>>>(V.pts, V.vel, mask, n_points, copy, vcopy, circ);
         else
-            cloud_sort_kernel<false><<<1, kSortThreads, 0, st>>>(V.pts, nullptr, mask, n_points, copy, nullptr);
+            cloud_sort_kernel<false><<<1, kSortThreads, 0, st>>>(V.pts, nullptr, mask, n_points, copy, nullptr, circ);
         if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
         V.pts = copy;
         V.vel = vcopy;
         V.mask = nullptr;
+        cc = circ;
     }
-    return launch_cycle(V, fp, st, sort);
+    return launch_cycle(V, fp, st, sort, cc);
 }
 
 // Clouds with point velocities go to mppi_predicted.cu.  Static clouds go to
 // the register-capped kernels of mppi_dense.cu when the sample grid exceeds
 // four blocks per SM and the footprint is small (a rectangle cover or at most
 // 16 edges: larger polygons need more registers than the cap leaves), else
-// to the uncapped ones here.
-int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl) {
-    if (V.vel) return launch_cycle_moving(V, fp, st, pdl);
+// to the unbounded ones here.
+int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ) {
+    if (V.vel) return launch_cycle_moving(V, fp, st, pdl, circ);
     static thread_local int sms = 0;
     if (sms <= 0) sms = current_sm_count();
     const bool small_fp = fp->kind == EXACT_FP_RECTS || fp->n_pad <= 16;
     if (small_fp && (long long)V.P.K * V.parts > 4LL * (sms > 0 ? sms : 148))
-        return launch_cycle_dense(V, fp, st, pdl);
-    return launch_cycle_t<false, 0>(V, fp, st, pdl);
+        return launch_cycle_dense(V, fp, st, pdl, circ);
+    return launch_cycle_t<false, 0>(V, fp, st, pdl, circ);
 }
 
 }  // namespace exact

@@ -369,6 +369,41 @@ __device__ __forceinline__ void sort_cloud_block(const float2 *__restrict__ pts,
     }
 }
 
+// Bounding circles (centre, radius, max speed) of the 64-point sub-chunks of
+// an ordered cloud in global memory, one warp per sub-chunk; the same values
+// chunk_circles computes for one staged pass, computed once per cycle.
+template <bool MOVING>
+__device__ __forceinline__ void cloud_circles(const float2 *__restrict__ pts, const float2 *__restrict__ vel, int N,
+                                              float4 *__restrict__ circ) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nsub = (N + kSub - 1) / kSub;
+    for (int s = warp; s < nsub; s += nwarps) {
+        float x[2], y[2], v2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = s * kSub + k * 32 + lane;
+            x[k] = y[k] = __int_as_float(0x7fffffff);
+            if (i < N) {
+                x[k] = pts[i].x; y[k] = pts[i].y;
+                if (MOVING && x[k] == x[k]) v2 = fmaxf(v2, fmaf(vel[i].x, vel[i].x, vel[i].y * vel[i].y));
+            }
+        }
+        float lx = warp_min_f(fminf(x[0], x[1])), ly = warp_min_f(fminf(y[0], y[1]));
+        float hx = -warp_min_f(-fmaxf(x[0], x[1])), hy = -warp_min_f(-fmaxf(y[0], y[1]));
+        const bool any = lx <= hx;
+        const float cx = 0.5f * (lx + hx), cy = 0.5f * (ly + hy);
+        float r2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (x[k] == x[k]) r2 = fmaxf(r2, fmaf(x[k] - cx, x[k] - cx, (y[k] - cy) * (y[k] - cy)));
+        r2 = -warp_min_f(-r2);
+        if (MOVING) v2 = -warp_min_f(-v2);
+        if (lane == 0)
+            circ[s] = any ? make_float4(cx, cy, sqrtf(r2) * 1.000001f, MOVING ? sqrtf(v2) * 1.000001f : 0.f)
+                          : make_float4(0.f, 0.f, -1.f, 0.f);
+    }
+}
+
 // ---------------------------------------------------------------- sample phase
 // Per-step minimum of the body-frame key over n staged points for the steps
 // [h0, h0 + nh) whose poses are in shared memory.  Masked points were staged
@@ -583,9 +618,13 @@ struct SampleSmem {
 // order), so the split never changes a bit of the result.  Ends with a
 // __syncthreads.  MOVING: V.vel holds the points' velocities and every step
 // sees the predicted cloud (see steps_min_keys).
+// circ: bounding circles of the 64-point sub-chunks of an ordered cloud
+// (cloud_circles), or NULL.  (Kept out of SceneView: a larger SceneView
+// parameter block made the compiler spill in the large-footprint kernels.)
 template <bool MOVING = false, class EV>
 __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, int r, int p, SampleSmem &sm,
-                                            float2 *s_pts, bool staged, int pairs_per_lane) {
+                                            float2 *s_pts, bool staged, int pairs_per_lane,
+                                            const float4 *circ = nullptr) {
     const MppiP &P = V.P;
     const int T = P.T, nu = P.nu, N = V.N;
     constexpr int kS = stage_points_of<MOVING>();
@@ -621,8 +660,14 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     }
     __syncthreads();
     const bool prune = !V.dmin && N >= kPruneMin;
+    // sub-chunk circles: copied from the ordered cloud's (64-point sub-chunks),
+    // or computed from the staged points
+    const bool pre_circ = circ != nullptr && pairs_per_lane == 1;
     if (!staged && prune) {
-        chunk_circles<MOVING>(s_pts, n0, sm.circ, pairs_per_lane);
+        if (pre_circ)
+            for (int s = threadIdx.x; s < (n0 + kSub - 1) / kSub; s += blockDim.x) sm.circ[s] = circ[s];
+        else
+            chunk_circles<MOVING>(s_pts, n0, sm.circ, pairs_per_lane);
         __syncthreads();
     }
     // without a d_min output the costs only need min(d_min, d_safe); clouds
@@ -636,7 +681,10 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
         stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, base, n, threadIdx.x, blockDim.x);
         __syncthreads();
         if (prune) {
-            chunk_circles<MOVING>(s_pts, n, sm.circ, pairs_per_lane);
+            if (pre_circ)
+                for (int s = threadIdx.x; s < (n + kSub - 1) / kSub; s += blockDim.x) sm.circ[s] = circ[base / kSub + s];
+            else
+                chunk_circles<MOVING>(s_pts, n, sm.circ, pairs_per_lane);
             __syncthreads();
         }
         steps_min_keys<MOVING>(ev, s_pts, n, sm.pose, sm.cw, h0, h1 - h0, sm.key, pairs_per_lane, sm.circ, cap,
@@ -775,7 +823,8 @@ struct ValidateSmem {
 // block scores the nominal exactly like a sample (Sec. III-E, IV-E; the cost
 // J_m of Algorithm 2) and empties the step keys.
 template <bool MOVING = false, class EV>
-__device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, int h, int c, ValidateSmem &sm) {
+__device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, int h, int c, ValidateSmem &sm,
+                                              const float4 *circ = nullptr) {
     const MppiP &P = V.P;
     const int K = P.K, T = P.T, nu = P.nu, TN = T * nu, G = V.upd_blocks;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -830,8 +879,21 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
     const int npairs = (N + 1) >> 1;
     const int pend = min(npairs, (c + 1) * kValChunkPairs);
     const float th = (float)(h + P.state_offset) * P.dt;   // time of the scored state (MOVING)
+    // ordered clouds: skip 64-point sub-chunks farther than d_safe from the
+    // footprint (the validation and the nominal's cost only need min(d, d_safe))
+    const float3 bc = ev.bound();
+    const float cwx = fmaf(qp.z, bc.x, fmaf(-qp.w, bc.y, qp.x)), cwy = fmaf(qp.w, bc.x, fmaf(qp.z, bc.y, qp.y));
+    const float vlim = fmaxf(P.d_safe, 0.f) + kPruneSlack + 1e-5f * (fabsf(cwx) + fabsf(cwy));
     float best = finf();
     for (int j = c * kValChunkPairs + tid; j < pend; j += kBlock) {
+        if (circ) {   // warp-uniform: the warp's 32 pairs are sub-chunk j / 32
+            const float4 cc = __ldg(circ + (j >> 5));
+            const float dx = cc.x - cwx, dy = cc.y - cwy;
+            float reach = cc.z + bc.z + 1e-5f * (fabsf(cc.x) + fabsf(cc.y));
+            if (MOVING) reach = fmaf(th, cc.w, reach);
+            const float far = reach + vlim;
+            if (cc.z < 0.f || fmaf(dx, dx, dy * dy) > far * far) continue;
+        }
         const int i0 = 2 * j, i1 = min(2 * j + 1, N - 1);
         float2 o0 = __ldg(V.pts + i0);
         float2 o1 = __ldg(V.pts + i1);

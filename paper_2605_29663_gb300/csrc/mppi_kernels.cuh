@@ -2,9 +2,9 @@
 // and their stream-ordered launch, templated on static / predicted
 // (time-indexed) obstacle points and on the sample kernel's minimum resident
 // blocks per SM (MINB).  MINB = 4 caps the sample kernel at 64 registers:
-// four blocks per SM, which pays when the grid spans several waves; with
-// few samples (one wave or less) the uncapped kernel (MINB = 0: no bound,
-// the compiler's own register choice) finishes sooner.  mppi.cu instantiates the static
+// four blocks per SM, which pays when the grid spans several waves and the
+// footprint is small; otherwise MINB = 2 (at most 128 registers: without a
+// bound the compiler may take all 255 and leave one block per SM).  mppi.cu instantiates the static
 // uncapped cycle, mppi_dense.cu the static capped one and mppi_predicted.cu
 // the predicted (capped) one, so the three compile in parallel.
 #pragma once
@@ -14,7 +14,7 @@ namespace exact {
 
 template <class FPC, bool MOVING, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB)
-mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev) {
+mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev, const float4 *circ) {
     extern __shared__ float2 s_pts[];   // min(N, stage) staged points (float4 each when MOVING)
     __shared__ SampleSmem sm;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -23,7 +23,7 @@ mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev) {
         V.hdr->ticket[1] = 0u;
         V.hdr->bad = 0;
     }
-    sample_body<MOVING>(V, ev, blockIdx.x / V.parts, blockIdx.x % V.parts, sm, s_pts, false, 1);
+    sample_body<MOVING>(V, ev, blockIdx.x / V.parts, blockIdx.x % V.parts, sm, s_pts, false, 1, circ);
 }
 
 template <bool MOVING>
@@ -33,23 +33,29 @@ __global__ void __launch_bounds__(kUpdBlock) mppi_update_kernel(const SceneView 
 }
 
 template <class FPC, bool MOVING>
-__global__ void __launch_bounds__(kBlock) mppi_validate_kernel(const SceneView V, const ConstEval<FPC> ev) {
+__global__ void __launch_bounds__(kBlock) mppi_validate_kernel(const SceneView V, const ConstEval<FPC> ev,
+                                                               const float4 *circ) {
     __shared__ ValidateSmem sm;
-    validate_body<MOVING>(V, ev, blockIdx.x / V.val_chunks, blockIdx.x % V.val_chunks, sm);
+    validate_body<MOVING>(V, ev, blockIdx.x / V.val_chunks, blockIdx.x % V.val_chunks, sm, circ);
 }
 
-// One block rewrites the cloud in spatial order (see sort_cloud_block).
+// One block rewrites the cloud in spatial order (see sort_cloud_block) and
+// takes the bounding circles of its 64-point sub-chunks.
 template <bool MOVING>
 __global__ void __launch_bounds__(kSortThreads)
-cloud_sort_kernel(const float2 *pts, const float2 *vel, const uint8_t *mask, int N, float2 *opts, float2 *ovel) {
+cloud_sort_kernel(const float2 *pts, const float2 *vel, const uint8_t *mask, int N, float2 *opts, float2 *ovel,
+                  float4 *circ) {
     __shared__ SortSmem sm;
     sort_cloud_block<MOVING>(pts, vel, mask, N, opts, ovel, sm);
+    __syncthreads();
+    cloud_circles<MOVING>(opts, ovel, N, circ);
 }
 
-// Bytes of the spatially ordered cloud copy (points, and velocities when
-// predicted) that follows a scene's scratch in the context arena.
+// Bytes of the spatially ordered cloud copy (points, velocities when
+// predicted, sub-chunk circles) that follows a scene's scratch in the arena.
 inline size_t cloud_copy_bytes(int N, bool moving) {
-    return align_up((size_t)N * sizeof(float2), 256) * (moving ? 2 : 1);
+    return align_up((size_t)N * sizeof(float2), 256) * (moving ? 2 : 1) +
+           align_up((size_t)((N + kSub - 1) / kSub) * sizeof(float4), 256);
 }
 
 
@@ -57,22 +63,23 @@ inline size_t cloud_copy_bytes(int N, bool moving) {
 // pdl: the sample kernel follows a cloud-ordering kernel and may start early
 // (its rollouts do not read the cloud; sample_body waits before staging).
 template <bool MOVING, int MINB>
-int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl = false) {
+int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl = false,
+                   const float4 *circ = nullptr) {
     const size_t smem = (size_t)min(V.N, stage_points_of<MOVING>()) * (MOVING ? sizeof(float4) : sizeof(float2));
     return with_footprint(fp, [&](auto fpc) -> int {
         using FPC = decltype(fpc);
         const ConstEval<FPC> ev{fpc};
         if (pdl) {
-            if (launch_dependent(mppi_sample_kernel<FPC, MOVING, MINB>, V.P.K * V.parts, kBlock, smem, st, V, ev) !=
+            if (launch_dependent(mppi_sample_kernel<FPC, MOVING, MINB>, V.P.K * V.parts, kBlock, smem, st, V, ev, circ) !=
                 cudaSuccess)
                 return EXACT_ECUDA;
         } else {
-            mppi_sample_kernel<FPC, MOVING, MINB><<<V.P.K * V.parts, kBlock, smem, st>>>(V, ev);
+            mppi_sample_kernel<FPC, MOVING, MINB><<<V.P.K * V.parts, kBlock, smem, st>>>(V, ev, circ);
             if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
         }
         if (launch_dependent(mppi_update_kernel<MOVING>, V.upd_blocks, kUpdBlock, 0, st, V) != cudaSuccess)
             return EXACT_ECUDA;
-        if (launch_dependent(mppi_validate_kernel<FPC, MOVING>, V.P.T * V.val_chunks, kBlock, 0, st, V, ev) !=
+        if (launch_dependent(mppi_validate_kernel<FPC, MOVING>, V.P.T * V.val_chunks, kBlock, 0, st, V, ev, circ) !=
             cudaSuccess)
             return EXACT_ECUDA;
         return EXACT_OK;
@@ -81,9 +88,10 @@ int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t s
 
 // Any cycle (mppi.cu: picks one of the three below), the static capped cycle
 // (mppi_dense.cu) and the predicted cycle (mppi_predicted.cu).
-int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl = false);
-int launch_cycle_dense(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl);
-int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl);
+int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl = false,
+                 const float4 *circ = nullptr);
+int launch_cycle_dense(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ);
+int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ);
 
 // mppi_step with optional point velocities (NULL: static cloud).
 int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const float *velocity,

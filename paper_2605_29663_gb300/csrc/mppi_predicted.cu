@@ -10,8 +10,9 @@
 
 namespace exact {
 
-int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl) {
-    return launch_cycle_t<true, 4>(V, fp, st, pdl);
+int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl,
+                        const float4 *circ) {
+    return launch_cycle_t<true, 4>(V, fp, st, pdl, circ);
 }
 
 }  // namespace exact
