@@ -179,3 +179,30 @@ def test_uniform_footprint_batch_equals_single_scene_bitwise(ex, kind):
         ref = _run_single(ex, ctx, s)
         for key in ("dmin", "costs", "weights", "U_upd", "U", "u_star"):
             np.testing.assert_array_equal(got[i][key], ref[key], err_msg=f"scene {i} {key}")
+
+
+def test_batched_ordered_clouds_change_no_cost(ex):
+    """Scenes of 1,024 points or more get spatially ordered copies (several
+    shared-memory passes for the largest): the batch without d_min outputs
+    matches the batch with them bit for bit, shuffled clouds included."""
+    import torch
+    g = synth.rng(17)
+    scenes = []
+    for i, N in enumerate([1100, 3000, 9000]):
+        s = synth.random_scene(g, [synth.DIFF, synth.ACKERMANN, synth.OMNI][i], 10, N, 160, 16, n_obst=50)
+        if i == 1:   # a shuffled cloud
+            perm = g.permutation(N)
+            s["cloud"] = np.ascontiguousarray(s["cloud"][perm])
+            s["mask"] = None if s["mask"] is None else np.ascontiguousarray(s["mask"][perm])
+        scenes.append(s)
+    res = []
+    for dmin in (True, False):
+        dev = [_dev_scene(ex, s) for s in scenes]
+        b = ex.Batch(dev, dmin=dmin)
+        b.step()
+        torch.cuda.synchronize()
+        res.append([dict({k: v.cpu().numpy() for k, v in o.items()}, U=d["U"].cpu().numpy())
+                    for d, o in zip(dev, b.outputs)])
+    for i in range(len(scenes)):
+        for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
+            np.testing.assert_array_equal(res[0][i][k], res[1][i][k], err_msg=f"scene {i} {k}")

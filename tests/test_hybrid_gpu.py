@@ -128,7 +128,7 @@ def test_hybrid_cycles_match_oracle(ex):
     Algorithm 1 outputs, the augmented costs and the selection are compared."""
     import torch
     g = synth.rng(77)
-    modes = synth.hybrid(3, K=256, T=16, N=900)
+    modes = synth.hybrid(3, K=256, T=16, N=1500)
     dev = _hybrid_dev(ex, modes)
     hp = dict(lambda_switch=2.0, cool_max=2)
     h = ex.Hybrid(dev, weights=True, **hp)

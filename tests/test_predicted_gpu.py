@@ -136,3 +136,23 @@ def test_pruning_with_predictions_changes_no_cost(ex, ctx):
         res.append(dict({k: v.cpu().numpy() for k, v in out.items()}, U=U.cpu().numpy()))
     for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
         np.testing.assert_array_equal(res[0][k], res[1][k], err_msg=k)
+
+
+def test_predicted_cloud_order_changes_nothing(ex, ctx):
+    """Points and velocities shuffled together give the same bits (the cycle
+    orders the cloud itself before pruning)."""
+    import torch
+    s = synth.dynamic_scene(12, K=256, T=20, N=2048)
+    perm = synth.rng(13).permutation(2048)
+    t = dict(s, cloud=np.ascontiguousarray(s["cloud"][perm]), vel=np.ascontiguousarray(s["vel"][perm]),
+             mask=None if s["mask"] is None else np.ascontiguousarray(s["mask"][perm]))
+    outs = []
+    for sc in (s, t):
+        fp = ex.Footprint(sc["kind"], sc["fp"])
+        U = _t(sc["U"].astype(np.float32))
+        out = ex.mppi_step(ctx, _t(sc["q0"]), _t(sc["cloud"]), _t(sc["waypoints"]), U, _t(sc["eps"]), fp,
+                           sc["params"], mask=None if sc["mask"] is None else _t(sc["mask"]), velocity=_t(sc["vel"]))
+        torch.cuda.synchronize()
+        outs.append(dict({k: v.cpu().numpy() for k, v in out.items()}, U=U.cpu().numpy()))
+    for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
+        np.testing.assert_array_equal(outs[0][k], outs[1][k], err_msg=k)
