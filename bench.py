@@ -43,8 +43,9 @@ L2_BYTES = 129 * 1024 * 1024
 # the headline kernel, from the ncu capture summarised in
 # profiles/sdf_batch_kernel_poly32_16384x8192.md, valid only while the kernel
 # sources hash to the recorded value (reported as null otherwise).
-TRAFFIC = {"sources": ["paper_2605_29663_gb300/csrc/sdf_batch.cu", "paper_2605_29663_gb300/csrc/common.cuh"],
-           "sha256_16": "74c696572c36d89f", "bytes_per_launch": 586496 + 476210688}
+TRAFFIC = {"sources": ["paper_2605_29663_gb300/csrc/sdf_batch.cu", "paper_2605_29663_gb300/csrc/common.cuh",
+                       "paper_2605_29663_gb300/csrc/internal.h"],
+           "sha256_16": "9838ee86e474e294", "bytes_per_launch": 576256 + 475673600}
 
 
 def measured_traffic():
@@ -606,13 +607,15 @@ def run_gpu(args):
     ex.load()
 
     w = synth.sdf_microbench(seed=rank)
+    P = args.sdf_poses   # fewer poses only for profiler captures of a small case
+    w["poses"] = w["poses"][:P]
     fp = ex.Footprint(w["kind"], w["fp"])
     ctx = ex.Context()
     pts = torch.from_numpy(w["points"]).to(dev)
     poses = torch.from_numpy(w["poses"]).to(dev)
-    d = torch.empty((N_POSES, N_POINTS), dtype=torch.float32, device=dev)
-    m = torch.empty(N_POSES, dtype=torch.float32, device=dev)
-    a = torch.empty(N_POSES, dtype=torch.int32, device=dev)
+    d = torch.empty((P, N_POINTS), dtype=torch.float32, device=dev)
+    m = torch.empty(P, dtype=torch.float32, device=dev)
+    a = torch.empty(P, dtype=torch.int32, device=dev)
     out = {"dist": d, "dmin": m, "argmin": a}
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -639,15 +642,15 @@ def run_gpu(args):
     torch.cuda.synchronize()
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = max_over_ranks(torch, dist, sum(per) / len(per), dev)
-    evals = N_POSES * N_POINTS * N_VERTS
+    evals = P * N_POINTS * N_VERTS
     value = whole_job_value(world, evals, ms)
 
     # end to end through the public call with host buffers: H2D of the step's
     # inputs from pinned memory, the call, D2H of the per-pose min / argmin
     h_pts = torch.from_numpy(w["points"]).pin_memory()
     h_poses = torch.from_numpy(w["poses"]).pin_memory()
-    h_m = torch.empty(N_POSES, dtype=torch.float32).pin_memory()
-    h_a = torch.empty(N_POSES, dtype=torch.int32).pin_memory()
+    h_m = torch.empty(P, dtype=torch.float32).pin_memory()
+    h_a = torch.empty(P, dtype=torch.int32).pin_memory()
     e_steps = max(3, min(args.steps, 10))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -675,20 +678,20 @@ def run_gpu(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak = fp32_peak_tflops(sm_max)
     achieved = FLOPS_PER_POINT_EDGE * evals / (ms * 1e-3) / 1e12
-    traffic = measured_traffic()
+    traffic = measured_traffic() if P == N_POSES else None
     line = {
         "metric": "SDF point-edge evals/s", "value": value, "unit": "point-edge evals/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"sdf_microbench: {N_POSES} poses x {N_POINTS} points x {N_VERTS}-vertex star "
+        "config": {"workload": f"sdf_microbench: {P} poses x {N_POINTS} points x {N_VERTS}-vertex star "
                                "polygon, full signed-distance matrix + per-pose min/argmin",
-                   "poses": N_POSES, "points": N_POINTS, "edges": N_VERTS, "seed": "rank",
+                   "poses": P, "points": N_POINTS, "edges": N_VERTS, "seed": "rank",
                    "l2": "flushed (2x L2 zero-fill) between timed iterations", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "sdf_batch_kernel<PolyC<32>, true, false>",
-                     "algorithmic_bytes_per_launch": N_POSES * N_POINTS * 4 + N_POINTS * 8 + N_POSES * 12,
+                     "algorithmic_bytes_per_launch": P * N_POINTS * 4 + N_POINTS * 8 + P * 12,
                      "flops_per_launch": FLOPS_PER_POINT_EDGE * evals,
                      "peak_basis": f"152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_max:.0f} MHz max SM clock "
                                    "(derived; MEASURED_PEAKS.json carries only HBM and bf16 figures)"},
@@ -722,6 +725,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the MPPI cycle measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target length of the CPU oracle sample")
+    ap.add_argument("--sdf-poses", type=int, default=N_POSES,
+                    help="poses of the sdf workload (fewer only to profile a small case)")
     ap.add_argument("--workload", choices=["sdf", "plain_step", "forklift", "predicted", "hybrid", "batched64"],
                     default="sdf",
                     help="sdf (headline) or one MPPI cycle workload timed on its own")

@@ -219,11 +219,15 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         D.nfp = fp->n_pad;
         D.bc = make_float3(fp->bcx, fp->bcy, fp->brad);
         if (fp->kind == EXACT_FP_POLYGON) {
-            for (int e = 0; e < fp->n_pad; ++e) {
-                D.fpc[2 * e] = make_float4(fp->vx[e], fp->vy[e], fp->exn[e], fp->eyn[e]);
-                D.fpc[2 * e + 1] = make_float4(fp->ex[e], fp->ey[e], fp->kx[e], 0.f);
+            const int E = fp->n_pad;
+            float *eyn = reinterpret_cast<float *>(D.fpc + 3 * E + 1);
+            for (int e = 0; e < E; ++e) {
+                D.fpc[3 * e] = make_float4(-fp->vx[e], -fp->vx[e], -fp->vy[e], -fp->vy[e]);
+                D.fpc[3 * e + 1] = make_float4(fp->exn[e], fp->exn[e], -fp->kx[e], -fp->kx[e]);
+                D.fpc[3 * e + 2] = make_float4(-fp->ex[e], -fp->ex[e], -fp->ey[e], -fp->ey[e]);
+                eyn[e] = fp->eyn[e];
             }
-            D.fpc[2 * fp->n_pad] = D.fpc[0];
+            D.fpc[3 * E] = D.fpc[0];
         } else {
             for (int j = 0; j < fp->n_pad; ++j) D.fpc[j] = make_float4(fp->cx[j], fp->cy[j], fp->sx[j], fp->sy[j]);
         }

@@ -7,7 +7,7 @@
 
 namespace exact {
 
-constexpr int kFpSlots = 2 * EXACT_MAX_POLY_VERTICES + 2;   // float4 footprint slots
+constexpr int kFpSlots = poly_slot_count(EXACT_MAX_POLY_VERTICES);   // float4 footprint slots
 constexpr size_t kHdrStride = 64;                            // bytes between scene headers
 
 struct SceneDev {
@@ -21,7 +21,7 @@ struct SceneDev {
 };
 
 __device__ __forceinline__ void load_fp(float4 *dst, const SceneDev &D) {
-    const int nf = D.kind == EXACT_FP_POLYGON ? 2 * D.nfp + 1 : D.nfp;
+    const int nf = D.kind == EXACT_FP_POLYGON ? poly_slot_count(D.nfp) : D.nfp;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) dst[i] = D.fpc[i];
 }
 

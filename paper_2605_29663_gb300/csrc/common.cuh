@@ -18,16 +18,25 @@ constexpr unsigned long long kNoKey = ~0ull;
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
 
+// Two FP32 lanes in one 64-bit register pair, for the packed f32x2
+// arithmetic of sm_100-class GPUs: one instruction does the same IEEE
+// round-to-nearest operation on both lanes, so a packed chain gives the
+// bits of the scalar chain it replaces while taking half the issue slots.
+typedef unsigned long long f2x;
+
 // Polygon footprint (Sec. IV-B.2) padded to E edges.  Padding vertices repeat
 // vertex 0, which adds zero-length edges: their clipped projection is 0 (the
 // distance to a vertex already covered) and both ends lie at the same height,
-// so they never toggle the crossing parity.
+// so they never toggle the crossing parity.  The edge terms are stored as
+// lane pairs (the same value in both lanes) for the packed evaluator, with
+// the signs folded in so that every step is an add, multiply or fma.
 template <int E>
 struct PolyC {
-    float vx[E], vy[E];     // vertices v_b
-    float exn[E], eyn[E];   // e_b / |e_b|^2   (0 for a zero-length edge)
-    float ex[E], ey[E];     // e_b = v_{b+1} - v_b
-    float kx[E];            // e_bx / e_by      (0 when e_by == 0)
+    f2x nvx[E], nvy[E];     // -v_b
+    f2x exn[E];             // e_bx / |e_b|^2   (0 for a zero-length edge)
+    f2x nex[E], ney[E];     // -e_b,  e_b = v_{b+1} - v_b
+    f2x nkx[E];             // -e_bx / e_by     (0 when e_by == 0)
+    float eyn[E];           // e_by / |e_b|^2   (scalar: its fma saturates)
     float bcx, bcy, brad;   // bounding circle: centre, radius (rounded up)
 };
 
@@ -48,7 +57,7 @@ __device__ __forceinline__ void body_frame(float ox, float oy, float tx, float t
 }
 
 // ---------------------------------------------------------------- polygon
-// Sec. IV-C.3 for two independent body-frame points.  Returns the squared
+// Sec. IV-C.3 for two body-frame points, one per lane.  Returns the squared
 // unsigned distance min_b d_seg,b^2 in m* and the crossing parity in the
 // sign bit of s*.
 //
@@ -57,8 +66,11 @@ __device__ __forceinline__ void body_frame(float ox, float oy, float tx, float t
 // end heights straddle p_y and the crossing lies right of p.  With
 // dy_b = p_y - v_by, "v_b above p" is the sign bit of dy_b, so the straddle
 // is the sign bit of dy_b * dy_{b+1}; the crossing abscissa test
-// p_x < v_bx + dy_b e_bx / e_by is the sign of g = dy_b k_b - dx_b being
-// clear.  Both ends of a vertex use the same dy, so the parity is consistent.
+// p_x < v_bx + dy_b e_bx / e_by holds when h = dx_b - dy_b k_b is negative
+// (k_b = e_bx / e_by), i.e. when the sign bit of h is set.  Both ends of a
+// vertex use the same dy, so every crossing is counted once.  A point exactly
+// on the crossing abscissa (h = 0) lies on the boundary, where either sign
+// is the exact distance 0.
 // Three-input minimum (one instruction on sm_100-class GPUs).
 __device__ __forceinline__ float fmin3(float a, float b, float c) {
     float r;
@@ -66,50 +78,77 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
     return r;
 }
 
+__device__ __forceinline__ f2x pack2(float lo, float hi) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f2x v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+    f2x r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+    f2x r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+    f2x r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 struct PolyAcc {
-    float dxa0, dya0, dxa1, dya1;   // p - v_b for the two points
-    float mm0, mm1;                 // running min of d_seg^2
-    unsigned ss0, ss1;              // crossing parity (sign bit)
+    f2x dxa, dya;           // p - v_b for the two points
+    float mm0, mm1;         // running min of d_seg^2
+    unsigned ss0, ss1;      // crossing parity (sign bit)
 };
 
-// Edge B (a compile-time index, so every footprint term is an immediate
-// constant-bank operand) for both points; returns the two squared segment
-// distances and advances the vertex differences to v_{B+1}.
+// Edge B (a compile-time index, so every footprint term is a constant-bank
+// operand) for both points; returns the two squared segment distances and
+// advances the vertex differences to v_{B+1}.  Only the clipped projection
+// runs per lane: f32x2 has no saturating form.
 template <int E, int B>
-__device__ __forceinline__ void poly_edge(const PolyC<E> &P, float px0, float py0, float px1, float py1,
-                                          const PolyAcc &z, PolyAcc &a, float &q0, float &q1) {
-    float dxb0, dyb0, dxb1, dyb1;
+__device__ __forceinline__ void poly_edge(const PolyC<E> &P, f2x PX, f2x PY, const PolyAcc &z, PolyAcc &a,
+                                          float &q0, float &q1) {
+    f2x dxb, dyb;
     if constexpr (B + 1 < E) {
-        dxb0 = px0 - P.vx[B + 1]; dyb0 = py0 - P.vy[B + 1];
-        dxb1 = px1 - P.vx[B + 1]; dyb1 = py1 - P.vy[B + 1];
+        dxb = add2(PX, P.nvx[B + 1]);
+        dyb = add2(PY, P.nvy[B + 1]);
     } else {
-        dxb0 = z.dxa0; dyb0 = z.dya0; dxb1 = z.dxa1; dyb1 = z.dya1;
+        dxb = z.dxa;
+        dyb = z.dya;
     }
-    const float t0 = __saturatef(fmaf(a.dya0, P.eyn[B], a.dxa0 * P.exn[B]));
-    const float t1 = __saturatef(fmaf(a.dya1, P.eyn[B], a.dxa1 * P.exn[B]));
-    const float qx0 = fmaf(-t0, P.ex[B], a.dxa0), qy0 = fmaf(-t0, P.ey[B], a.dya0);
-    const float qx1 = fmaf(-t1, P.ex[B], a.dxa1), qy1 = fmaf(-t1, P.ey[B], a.dya1);
-    q0 = fmaf(qy0, qy0, qx0 * qx0);
-    q1 = fmaf(qy1, qy1, qx1 * qx1);
-    const float g0 = fmaf(a.dya0, P.kx[B], -a.dxa0), g1 = fmaf(a.dya1, P.kx[B], -a.dxa1);
-    const float X0 = a.dya0 * dyb0, X1 = a.dya1 * dyb1;
-    a.ss0 ^= __float_as_uint(X0) & ~__float_as_uint(g0);
-    a.ss1 ^= __float_as_uint(X1) & ~__float_as_uint(g1);
-    a.dxa0 = dxb0; a.dya0 = dyb0; a.dxa1 = dxb1; a.dya1 = dyb1;
+    float u0, u1, dy0, dy1;
+    unpack2(mul2(a.dxa, P.exn[B]), u0, u1);
+    unpack2(a.dya, dy0, dy1);
+    const f2x t = pack2(__saturatef(fmaf(dy0, P.eyn[B], u0)), __saturatef(fmaf(dy1, P.eyn[B], u1)));
+    const f2x qx = fma2(t, P.nex[B], a.dxa), qy = fma2(t, P.ney[B], a.dya);
+    unpack2(fma2(qy, qy, mul2(qx, qx)), q0, q1);
+    float h0, h1, x0, x1;
+    unpack2(fma2(a.dya, P.nkx[B], a.dxa), h0, h1);
+    unpack2(mul2(a.dya, dyb), x0, x1);
+    a.ss0 ^= __float_as_uint(x0) & __float_as_uint(h0);
+    a.ss1 ^= __float_as_uint(x1) & __float_as_uint(h1);
+    a.dxa = dxb;
+    a.dya = dyb;
 }
 
 // Edges B and B+1 (E is even), folded into the running minimum with one
 // three-input min per point; recursion unrolls all E edges.
 template <int E, int B>
-__device__ __forceinline__ void poly_edges(const PolyC<E> &P, float px0, float py0, float px1, float py1,
-                                           const PolyAcc &z, PolyAcc &a) {
+__device__ __forceinline__ void poly_edges(const PolyC<E> &P, f2x PX, f2x PY, const PolyAcc &z, PolyAcc &a) {
     if constexpr (B < E) {
         float qa0, qa1, qb0, qb1;
-        poly_edge<E, B>(P, px0, py0, px1, py1, z, a, qa0, qa1);
-        poly_edge<E, B + 1>(P, px0, py0, px1, py1, z, a, qb0, qb1);
+        poly_edge<E, B>(P, PX, PY, z, a, qa0, qa1);
+        poly_edge<E, B + 1>(P, PX, PY, z, a, qb0, qb1);
         a.mm0 = fmin3(a.mm0, qa0, qb0);
         a.mm1 = fmin3(a.mm1, qa1, qb1);
-        poly_edges<E, B + 2>(P, px0, py0, px1, py1, z, a);
+        poly_edges<E, B + 2>(P, PX, PY, z, a);
     }
 }
 
@@ -117,13 +156,14 @@ template <int E>
 __device__ __forceinline__ void poly_eval2(const PolyC<E> &P, float px0, float py0, float px1, float py1,
                                            float &m0, float &m1, unsigned &s0, unsigned &s1) {
     static_assert(E % 2 == 0, "edge count is padded to an even number");
+    const f2x PX = pack2(px0, px1), PY = pack2(py0, py1);
     PolyAcc z;
-    z.dxa0 = px0 - P.vx[0]; z.dya0 = py0 - P.vy[0];
-    z.dxa1 = px1 - P.vx[0]; z.dya1 = py1 - P.vy[0];
+    z.dxa = add2(PX, P.nvx[0]);
+    z.dya = add2(PY, P.nvy[0]);
     z.mm0 = z.mm1 = finf();
     z.ss0 = z.ss1 = 0u;
     PolyAcc a = z;
-    poly_edges<E, 0>(P, px0, py0, px1, py1, z, a);
+    poly_edges<E, 0>(P, PX, PY, z, a);
     m0 = a.mm0; m1 = a.mm1; s0 = a.ss0; s1 = a.ss1;
 }
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "common.cuh"
 #include "exact_mppi.h"
@@ -54,11 +55,17 @@ struct ArenaHeader {
 template <int E>
 inline PolyC<E> make_poly(const exact_footprint *fp) {
     PolyC<E> P;
+    // the same float in both lanes of a pair
+    auto both = [](float f) {
+        uint32_t u;
+        memcpy(&u, &f, sizeof u);
+        return ((unsigned long long)u << 32) | u;
+    };
     for (int b = 0; b < E; ++b) {
-        P.vx[b] = fp->vx[b]; P.vy[b] = fp->vy[b];
-        P.exn[b] = fp->exn[b]; P.eyn[b] = fp->eyn[b];
-        P.ex[b] = fp->ex[b]; P.ey[b] = fp->ey[b];
-        P.kx[b] = fp->kx[b];
+        P.nvx[b] = both(-fp->vx[b]); P.nvy[b] = both(-fp->vy[b]);
+        P.exn[b] = both(fp->exn[b]); P.eyn[b] = fp->eyn[b];
+        P.nex[b] = both(-fp->ex[b]); P.ney[b] = both(-fp->ey[b]);
+        P.nkx[b] = both(-fp->kx[b]);
     }
     P.bcx = fp->bcx; P.bcy = fp->bcy; P.brad = fp->brad;
     return P;

@@ -152,6 +152,7 @@ __device__ __forceinline__ double ord2d(unsigned long long u) {
 // ---------------------------------------------------------------- evaluators
 template <class FPC>
 struct ConstEval {            // footprint constants in the kernel parameters
+    static constexpr bool kQuad = false;   // no loads to share: two points per call
     FPC f;
     __device__ __forceinline__ void eval2(float px0, float py0, float px1, float py1, float &k0, float &k1) const {
         exact::eval2(f, px0, py0, px1, py1, k0, k1);
@@ -161,67 +162,105 @@ struct ConstEval {            // footprint constants in the kernel parameters
 };
 
 // Footprint constants in shared memory with a run-time edge / box count.
-// Polygon: C[2b] = (v_bx, v_by, e_bx/|e_b|^2, e_by/|e_b|^2),
-// C[2b+1] = (e_bx, e_by, e_bx/e_by, 0) for b < E, and C[2E] = C[0] (the
-// closing vertex).  Rects: C[j] = (cx, cy, sx, sy).  The arithmetic is the
-// same sequence of operations as the compile-time evaluators, so both give
-// identical keys.
+// Polygon (E edges), as lane pairs (the same value twice):
+//   C[3b]   = (-v_bx, -v_bx, -v_by, -v_by)                 b <= E, v_E = v_0
+//   C[3b+1] = (e_bx/|e_b|^2 twice, -e_bx/e_by twice)       b < E
+//   C[3b+2] = (-e_bx, -e_bx, -e_by, -e_by)                 b < E
+// then the E scalars e_by/|e_b|^2 from C[3E+1] on.  Rects: C[j] = (cx, cy,
+// sx, sy).  The arithmetic is the same sequence of operations as the
+// compile-time evaluators, so both give identical keys.
+__host__ __device__ constexpr int poly_slot_count(int E) { return 3 * E + 1 + (E + 3) / 4; }
+
 struct SmemEval {
+    static constexpr bool kQuad = true;   // eval4 shares each constant load among four points
     const float4 *C;
     int kind, n;
     float3 bc;    // bounding circle of the footprint (centre, radius)
     __device__ __forceinline__ float3 bound() const { return bc; }
-    __device__ __forceinline__ void eval2(float px0, float py0, float px1, float py1, float &k0, float &k1) const {
+
+    // NP lane pairs of points (px[2i], px[2i+1]) against every edge / box;
+    // each slot is read once for all of them.
+    template <int NP>
+    __device__ __forceinline__ void evaln(const float *px, const float *py, float *k) const {
         if (kind == EXACT_FP_POLYGON) {
-            float4 c = C[0];
-            float dxa0 = px0 - c.x, dya0 = py0 - c.y, dxa1 = px1 - c.x, dya1 = py1 - c.y;
-            float m0 = finf(), m1 = finf();
-            unsigned s0 = 0u, s1 = 0u;
-            // one edge for both points: squared segment distances, parity
+            // the packed evaluator of poly_eval2 with a run-time edge loop
+            // over the slot table of poly_slot_count
+            const ulonglong2 *S = reinterpret_cast<const ulonglong2 *>(C);
+            const float *eyn = reinterpret_cast<const float *>(C + 3 * n + 1);
+            const ulonglong2 v0 = S[0];
+            f2x PX[NP], PY[NP], dxa[NP], dya[NP];
+            float m[2 * NP];
+            unsigned sg[2 * NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                PX[i] = pack2(px[2 * i], px[2 * i + 1]);
+                PY[i] = pack2(py[2 * i], py[2 * i + 1]);
+                dxa[i] = add2(PX[i], v0.x);
+                dya[i] = add2(PY[i], v0.y);
+                m[2 * i] = m[2 * i + 1] = finf();
+                sg[2 * i] = sg[2 * i + 1] = 0u;
+            }
+            // one edge for every pair: squared segment distances, parity
             // toggles, and the differences advanced to the next vertex
-            auto edge = [&](const float4 &e, const float4 &nx, float &q0, float &q1) {
-                const float dxb0 = px0 - nx.x, dyb0 = py0 - nx.y, dxb1 = px1 - nx.x, dyb1 = py1 - nx.y;
-                const float t0 = __saturatef(fmaf(dya0, c.w, dxa0 * c.z));
-                const float t1 = __saturatef(fmaf(dya1, c.w, dxa1 * c.z));
-                const float qx0 = fmaf(-t0, e.x, dxa0), qy0 = fmaf(-t0, e.y, dya0);
-                const float qx1 = fmaf(-t1, e.x, dxa1), qy1 = fmaf(-t1, e.y, dya1);
-                q0 = fmaf(qy0, qy0, qx0 * qx0);
-                q1 = fmaf(qy1, qy1, qx1 * qx1);
-                const float g0 = fmaf(dya0, e.z, -dxa0), g1 = fmaf(dya1, e.z, -dxa1);
-                const float X0 = dya0 * dyb0, X1 = dya1 * dyb1;
-                s0 ^= __float_as_uint(X0) & ~__float_as_uint(g0);
-                s1 ^= __float_as_uint(X1) & ~__float_as_uint(g1);
-                dxa0 = dxb0; dya0 = dyb0; dxa1 = dxb1; dya1 = dyb1;
-                c = nx;
+            auto edge = [&](int b, float ey, float *q) {
+                const ulonglong2 kn = S[3 * b + 1], ne = S[3 * b + 2], vn = S[3 * b + 3];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    const f2x dxb = add2(PX[i], vn.x), dyb = add2(PY[i], vn.y);
+                    float u0, u1, dy0, dy1;
+                    unpack2(mul2(dxa[i], kn.x), u0, u1);
+                    unpack2(dya[i], dy0, dy1);
+                    const f2x t = pack2(__saturatef(fmaf(dy0, ey, u0)), __saturatef(fmaf(dy1, ey, u1)));
+                    const f2x qx = fma2(t, ne.x, dxa[i]), qy = fma2(t, ne.y, dya[i]);
+                    unpack2(fma2(qy, qy, mul2(qx, qx)), q[2 * i], q[2 * i + 1]);
+                    float h0, h1, x0, x1;
+                    unpack2(fma2(dya[i], kn.y, dxa[i]), h0, h1);
+                    unpack2(mul2(dya[i], dyb), x0, x1);
+                    sg[2 * i] ^= __float_as_uint(x0) & __float_as_uint(h0);
+                    sg[2 * i + 1] ^= __float_as_uint(x1) & __float_as_uint(h1);
+                    dxa[i] = dxb;
+                    dya[i] = dyb;
+                }
             };
             // the edge count is padded to an even number: two edges per
             // step, folded with one three-input minimum per point
             for (int b = 0; b < n; b += 2) {
-                const float4 ea = C[2 * b + 1], na = C[2 * b + 2], eb = C[2 * b + 3], nb = C[2 * b + 4];
-                float qa0, qa1, qb0, qb1;
-                edge(ea, na, qa0, qa1);
-                edge(eb, nb, qb0, qb1);
-                m0 = fmin3(m0, qa0, qb0);
-                m1 = fmin3(m1, qa1, qb1);
+                const float2 ey = *reinterpret_cast<const float2 *>(eyn + b);
+                float qa[2 * NP], qb[2 * NP];
+                edge(b, ey.x, qa);
+                edge(b + 1, ey.y, qb);
+#pragma unroll
+                for (int i = 0; i < 2 * NP; ++i) m[i] = fmin3(m[i], qa[i], qb[i]);
             }
-            k0 = __uint_as_float(__float_as_uint(m0) | (s0 & 0x80000000u));
-            k1 = __uint_as_float(__float_as_uint(m1) | (s1 & 0x80000000u));
+#pragma unroll
+            for (int i = 0; i < 2 * NP; ++i) k[i] = __uint_as_float(__float_as_uint(m[i]) | (sg[i] & 0x80000000u));
         } else {
-            float n0 = finf(), n1 = finf(), i0 = finf(), i1 = finf();
+            float nn[2 * NP], in[2 * NP];
+#pragma unroll
+            for (int i = 0; i < 2 * NP; ++i) nn[i] = in[i] = finf();
             for (int j = 0; j < n; ++j) {
                 const float4 q = C[j];
-                const float ax0 = fabsf(px0 - q.x) - q.z, ay0 = fabsf(py0 - q.y) - q.w;
-                const float ax1 = fabsf(px1 - q.x) - q.z, ay1 = fabsf(py1 - q.y) - q.w;
-                const float ux0 = ax0 + fabsf(ax0), uy0 = ay0 + fabsf(ay0);
-                const float ux1 = ax1 + fabsf(ax1), uy1 = ay1 + fabsf(ay1);
-                n0 = fminf(n0, fmaf(uy0, uy0, ux0 * ux0));
-                n1 = fminf(n1, fmaf(uy1, uy1, ux1 * ux1));
-                i0 = fminf(i0, fmaxf(ax0, ay0));
-                i1 = fminf(i1, fmaxf(ax1, ay1));
+#pragma unroll
+                for (int i = 0; i < 2 * NP; ++i) {
+                    const float ax = fabsf(px[i] - q.x) - q.z, ay = fabsf(py[i] - q.y) - q.w;
+                    const float ux = ax + fabsf(ax), uy = ay + fabsf(ay);
+                    nn[i] = fminf(nn[i], fmaf(uy, uy, ux * ux));
+                    in[i] = fminf(in[i], fmaxf(ax, ay));
+                }
             }
-            k0 = rect_key(n0, i0);
-            k1 = rect_key(n1, i1);
+#pragma unroll
+            for (int i = 0; i < 2 * NP; ++i) k[i] = rect_key(nn[i], in[i]);
         }
+    }
+    __device__ __forceinline__ void eval2(float px0, float py0, float px1, float py1, float &k0, float &k1) const {
+        const float px[2] = {px0, px1}, py[2] = {py0, py1};
+        float k[2];
+        evaln<1>(px, py, k);
+        k0 = k[0];
+        k1 = k[1];
+    }
+    __device__ __forceinline__ void eval4(const float (&px)[4], const float (&py)[4], float (&k)[4]) const {
+        evaln<2>(px, py, k);
     }
     __device__ __forceinline__ float dist(float key) const {
         if (kind == EXACT_FP_POLYGON) {
@@ -436,6 +475,24 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
     const int npairs = (n + 1) >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nsub = (n + kSub * ppl - 1) / (kSub * ppl);
+    // pair j (points 2j, 2j+1; an odd tail repeats the last point) in the
+    // body frame of step h
+    auto pair_at = [&](int j, int h, float &px0, float &py0, float &px1, float &py1) {
+        const float4 q = pose[h];
+        float2 o0, o1;
+        if constexpr (MOVING) {
+            const float th = cw[h].z;
+            const float4 *p4 = reinterpret_cast<const float4 *>(pts);
+            const float4 a0 = p4[2 * j], a1 = p4[min(2 * j + 1, n - 1)];
+            o0 = make_float2(fmaf(th, a0.z, a0.x), fmaf(th, a0.w, a0.y));
+            o1 = make_float2(fmaf(th, a1.z, a1.x), fmaf(th, a1.w, a1.y));
+        } else {
+            o0 = pts[2 * j];
+            o1 = pts[min(2 * j + 1, n - 1)];
+        }
+        body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
+        body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
+    };
     if (cap < 0.f) {
         const int span = 32 * 4;   // pairs per item
         const int nchunk = npairs > 0 ? (npairs + span - 1) / span : 0;
@@ -447,6 +504,20 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
             const float th = cw[h].z;
             float best = finf();
             const int jend = min(npairs, (c + 1) * span);
+            if constexpr (EV::kQuad) {
+                for (int j = c * span + lane; j < jend; j += 64) {
+                    const bool two = j + 32 < jend;
+                    float px[4], py[4], k[4];
+                    pair_at(j, h, px[0], py[0], px[1], py[1]);
+                    pair_at(two ? j + 32 : j, h, px[2], py[2], px[3], py[3]);
+                    ev.eval4(px, py, k);
+                    best = fmin3(best, k[0], k[1]);
+                    if (two) best = fmin3(best, k[2], k[3]);
+                }
+                best = warp_min_f(best);
+                if (lane == 0) atomicMin(keyh + h, f2ord(best));
+                continue;
+            }
             for (int j = c * span + lane; j < jend; j += 32) {
                 float2 o0, o1;
                 if constexpr (MOVING) {
@@ -521,6 +592,55 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
     int hh = lo;
     unsigned long long m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
     for (int k = pre[hh]; k < e0; ++k) m &= m - 1ull;
+    if constexpr (EV::kQuad) {
+        // units of one pair per lane -- (step, sub-chunk, i-th of its ppl
+        // pairs for this lane) -- in list order, two units per evaluation;
+        // each step's minimum is folded when the units move to another step
+        int e = e0, i = ppl, cs = 0, ch = 0;
+        auto next = [&](int &uh, int &uj) -> bool {
+            if (i == ppl) {
+                if (e >= e1) return false;
+                while (m == 0ull) {
+                    ++hh;
+                    m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
+                }
+                cs = __ffsll((long long)m) - 1;
+                m &= m - 1ull;
+                ++e;
+                ch = hh;
+                i = 0;
+            }
+            uh = ch;
+            uj = (cs * ppl + i) * 32 + lane;
+            ++i;
+            return true;
+        };
+        float best = finf();
+        int bh = -1;
+        auto fold = [&](int uh, float k) {
+            if (uh != bh) {   // warp-uniform
+                best = warp_min_f(best);
+                if (lane == 0 && bh >= 0 && best < finf()) atomicMin(keyh + h0 + bh, f2ord(best));
+                best = finf();
+                bh = uh;
+            }
+            best = fminf(best, k);
+        };
+        int ha, ja, hb, jb;
+        while (next(ha, ja)) {
+            const bool two = next(hb, jb);
+            if (!two) { hb = ha; jb = ja; }
+            const bool va = ja < npairs, vb = two && jb < npairs;
+            float px[4], py[4], k[4];
+            pair_at(va ? ja : npairs - 1, h0 + ha, px[0], py[0], px[1], py[1]);
+            pair_at(vb ? jb : npairs - 1, h0 + hb, px[2], py[2], px[3], py[3]);
+            ev.eval4(px, py, k);
+            fold(ha, va ? fminf(k[0], k[1]) : finf());
+            if (two) fold(hb, vb ? fminf(k[2], k[3]) : finf());
+        }
+        fold(-1, finf());
+        return;
+    }
     float best = finf();
     for (int e = e0; e < e1; ++e) {
         while (m == 0ull) {   // step done: fold its minimum, move to the next step with entries
