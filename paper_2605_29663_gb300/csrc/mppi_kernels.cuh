@@ -3,10 +3,12 @@
 // (time-indexed) obstacle points and on the sample kernel's minimum resident
 // blocks per SM (MINB).  MINB = 4 caps the sample kernel at 64 registers:
 // four blocks per SM, which pays when the grid spans several waves and the
-// footprint is small; otherwise MINB = 2 (at most 128 registers: without a
-// bound the compiler may take all 255 and leave one block per SM).  mppi.cu instantiates the static
-// uncapped cycle, mppi_dense.cu the static capped one and mppi_predicted.cu
-// the predicted (capped) one, so the three compile in parallel.
+// footprint is small; otherwise MINB = 0 leaves the register count to the
+// compiler (about 120 for these bodies; an explicit minimum of one or two
+// blocks changed its choices and measured slower, and so did 512-thread
+// blocks for small grids).  mppi.cu instantiates the static uncapped cycle,
+// mppi_dense.cu the static capped one and mppi_predicted.cu the predicted
+// (capped) one, so the three compile in parallel.
 #pragma once
 #include "mppi_cycle.cuh"
 
