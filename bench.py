@@ -35,6 +35,11 @@ if ROOT not in sys.path:
 
 N_POSES, N_POINTS, N_VERTS = 16384, 8192, 32
 FLOPS_PER_POINT_EDGE = 17      # canonical count, FMA = 2
+# what the polygon kernel executes per point-edge: the distance pass (dx, dy
+# 2; projection 3; q 4; |q|^2 3; min 1) for every point, the parity pass
+# (dx, dy 2; crossing abscissa 2; straddle product 1) only for points within
+# the footprint's bounding circle
+EXEC_FLOPS_DIST, EXEC_FLOPS_PARITY = 13, 5
 FLOPS_PER_POINT_BOX = 12
 L2_BYTES = 129 * 1024 * 1024
 
@@ -45,7 +50,7 @@ L2_BYTES = 129 * 1024 * 1024
 # sources hash to the recorded value (reported as null otherwise).
 TRAFFIC = {"sources": ["paper_2605_29663_gb300/csrc/sdf_batch.cu", "paper_2605_29663_gb300/csrc/common.cuh",
                        "paper_2605_29663_gb300/csrc/internal.h"],
-           "sha256_16": "9838ee86e474e294", "bytes_per_launch": 576256 + 475673600}
+           "sha256_16": "d7e1edadf1018c63", "bytes_per_launch": 396288 + 478070784}
 
 
 def measured_traffic():
@@ -55,6 +60,24 @@ def measured_traffic():
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return TRAFFIC["bytes_per_launch"] if h.hexdigest()[:16] == TRAFFIC["sha256_16"] else None
+
+
+def near_fraction(w, n_poses: int = 1024) -> float:
+    """Fraction of (pose, point) pairs of the sdf workload whose point lies
+    within the footprint's bounding circle (centre of the vertex bounding
+    box, radius to the farthest vertex) in the body frame: the pairs that
+    take the parity pass.  Float64, over the first n_poses poses."""
+    import numpy as np
+    v = np.asarray(w["fp"], np.float64)
+    c = 0.5 * (v.min(axis=0) + v.max(axis=0))
+    r = np.sqrt(((v - c) ** 2).sum(axis=1)).max()
+    poses = np.asarray(w["poses"][:n_poses], np.float64)
+    pts = np.asarray(w["points"], np.float64)
+    cs, sn = np.cos(poses[:, 2:3]), np.sin(poses[:, 2:3])
+    dx = pts[None, :, 0] - poses[:, 0:1]
+    dy = pts[None, :, 1] - poses[:, 1:2]
+    bx, by = cs * dx + sn * dy, -sn * dx + cs * dy
+    return float((((bx - c[0]) ** 2 + (by - c[1]) ** 2) <= r * r).mean())
 
 
 def max_over_ranks(torch, dist, ms: float, dev) -> float:
@@ -678,6 +701,8 @@ def run_gpu(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak = fp32_peak_tflops(sm_max)
     achieved = FLOPS_PER_POINT_EDGE * evals / (ms * 1e-3) / 1e12
+    near_f = near_fraction(w)
+    exec_tflops = (EXEC_FLOPS_DIST + EXEC_FLOPS_PARITY * near_f) * evals / (ms * 1e-3) / 1e12
     traffic = measured_traffic() if P == N_POSES else None
     line = {
         "metric": "SDF point-edge evals/s", "value": value, "unit": "point-edge evals/s",
@@ -693,6 +718,13 @@ def run_gpu(args):
                      "kernel": "sdf_batch_kernel<PolyC<32>, true, false>",
                      "algorithmic_bytes_per_launch": P * N_POINTS * 4 + N_POINTS * 8 + P * 12,
                      "flops_per_launch": FLOPS_PER_POINT_EDGE * evals,
+                     "executed": {"near_fraction": near_f,
+                                  "flops_per_point_edge": EXEC_FLOPS_DIST + EXEC_FLOPS_PARITY * near_f,
+                                  "tflops": exec_tflops, "frac": exec_tflops / peak,
+                                  "note": "achieved/frac count the canonical 17 flops per point-edge; the kernel "
+                                          "takes the crossing parity only for points within the footprint's "
+                                          "bounding circle (all others are outside, sign +), so it executes "
+                                          "fewer; outputs are the same bits either way"},
                      "peak_basis": f"152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_max:.0f} MHz max SM clock "
                                    "(derived; MEASURED_PEAKS.json carries only HBM and bf16 figures)"},
         "e2e": {"value": e2e_val, "unit": "point-edge evals/s", "h2d_bytes_per_step": h2d,

@@ -108,51 +108,64 @@ struct PolyAcc {
     unsigned ss0, ss1;      // crossing parity (sign bit)
 };
 
+// What an edge pass computes: the squared segment distances (kDist), the
+// crossing parity (kSign), or both.
+constexpr int kDist = 1, kSign = 2;
+
 // Edge B (a compile-time index, so every footprint term is a constant-bank
 // operand) for both points; returns the two squared segment distances and
 // advances the vertex differences to v_{B+1}.  Only the clipped projection
 // runs per lane: f32x2 has no saturating form.
-template <int E, int B>
+template <int E, int B, int PART>
 __device__ __forceinline__ void poly_edge(const PolyC<E> &P, f2x PX, f2x PY, const PolyAcc &z, PolyAcc &a,
                                           float &q0, float &q1) {
     f2x dxb, dyb;
     if constexpr (B + 1 < E) {
-        dxb = add2(PX, P.nvx[B + 1]);
+        if constexpr (PART & kDist) dxb = add2(PX, P.nvx[B + 1]);
         dyb = add2(PY, P.nvy[B + 1]);
     } else {
         dxb = z.dxa;
         dyb = z.dya;
     }
-    float u0, u1, dy0, dy1;
-    unpack2(mul2(a.dxa, P.exn[B]), u0, u1);
-    unpack2(a.dya, dy0, dy1);
-    const f2x t = pack2(__saturatef(fmaf(dy0, P.eyn[B], u0)), __saturatef(fmaf(dy1, P.eyn[B], u1)));
-    const f2x qx = fma2(t, P.nex[B], a.dxa), qy = fma2(t, P.ney[B], a.dya);
-    unpack2(fma2(qy, qy, mul2(qx, qx)), q0, q1);
-    float h0, h1, x0, x1;
-    unpack2(fma2(a.dya, P.nkx[B], a.dxa), h0, h1);
-    unpack2(mul2(a.dya, dyb), x0, x1);
-    a.ss0 ^= __float_as_uint(x0) & __float_as_uint(h0);
-    a.ss1 ^= __float_as_uint(x1) & __float_as_uint(h1);
+    if constexpr (PART & kDist) {
+        float u0, u1, dy0, dy1;
+        unpack2(mul2(a.dxa, P.exn[B]), u0, u1);
+        unpack2(a.dya, dy0, dy1);
+        const f2x t = pack2(__saturatef(fmaf(dy0, P.eyn[B], u0)), __saturatef(fmaf(dy1, P.eyn[B], u1)));
+        const f2x qx = fma2(t, P.nex[B], a.dxa), qy = fma2(t, P.ney[B], a.dya);
+        unpack2(fma2(qy, qy, mul2(qx, qx)), q0, q1);
+    }
+    if constexpr (PART & kSign) {
+        if constexpr (!(PART & kDist) && B + 1 < E) dxb = add2(PX, P.nvx[B + 1]);
+        float h0, h1, x0, x1;
+        unpack2(fma2(a.dya, P.nkx[B], a.dxa), h0, h1);
+        unpack2(mul2(a.dya, dyb), x0, x1);
+        a.ss0 ^= __float_as_uint(x0) & __float_as_uint(h0);
+        a.ss1 ^= __float_as_uint(x1) & __float_as_uint(h1);
+    }
     a.dxa = dxb;
     a.dya = dyb;
 }
 
 // Edges B and B+1 (E is even), folded into the running minimum with one
 // three-input min per point; recursion unrolls all E edges.
-template <int E, int B>
+template <int E, int B, int PART>
 __device__ __forceinline__ void poly_edges(const PolyC<E> &P, f2x PX, f2x PY, const PolyAcc &z, PolyAcc &a) {
     if constexpr (B < E) {
         float qa0, qa1, qb0, qb1;
-        poly_edge<E, B>(P, PX, PY, z, a, qa0, qa1);
-        poly_edge<E, B + 1>(P, PX, PY, z, a, qb0, qb1);
-        a.mm0 = fmin3(a.mm0, qa0, qb0);
-        a.mm1 = fmin3(a.mm1, qa1, qb1);
-        poly_edges<E, B + 2>(P, PX, PY, z, a);
+        poly_edge<E, B, PART>(P, PX, PY, z, a, qa0, qa1);
+        poly_edge<E, B + 1, PART>(P, PX, PY, z, a, qb0, qb1);
+        if constexpr (PART & kDist) {
+            a.mm0 = fmin3(a.mm0, qa0, qb0);
+            a.mm1 = fmin3(a.mm1, qa1, qb1);
+        }
+        poly_edges<E, B + 2, PART>(P, PX, PY, z, a);
     }
 }
 
-template <int E>
+// The parts PART of the evaluation for two points: each part takes the same
+// operations as in the full evaluation, so its results are the same bits.
+template <int E, int PART = kDist | kSign>
 __device__ __forceinline__ void poly_eval2(const PolyC<E> &P, float px0, float py0, float px1, float py1,
                                            float &m0, float &m1, unsigned &s0, unsigned &s1) {
     static_assert(E % 2 == 0, "edge count is padded to an even number");
@@ -163,7 +176,7 @@ __device__ __forceinline__ void poly_eval2(const PolyC<E> &P, float px0, float p
     z.mm0 = z.mm1 = finf();
     z.ss0 = z.ss1 = 0u;
     PolyAcc a = z;
-    poly_edges<E, 0>(P, PX, PY, z, a);
+    poly_edges<E, 0, PART>(P, PX, PY, z, a);
     m0 = a.mm0; m1 = a.mm1; s0 = a.ss0; s1 = a.ss1;
 }
 

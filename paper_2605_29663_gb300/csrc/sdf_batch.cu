@@ -13,6 +13,117 @@
 
 namespace exact {
 
+constexpr int kNearQ = 128;   // per-warp queue of near points (two batches)
+
+// Polygon rows: point pairs [pbeg, pend) of one pose.  The edge loop takes
+// the distances only.  The crossing parity can be odd only for a point within
+// the footprint's bounding circle; every other point is outside, sign +.
+// Points within the circle (plus a margin far above the rounding of the
+// parity test, so that the skipped parities are exactly the even ones the
+// full evaluation would find) are queued per warp in index order with their
+// squared distance, and take a parity-only pass over the edges 64 at a time.
+// Those found inside get their distance rewritten with the minus sign (after
+// a __syncwarp, which orders the two stores).  Both passes repeat the
+// operations of the full evaluation, so every output is the same bits.  The
+// per-thread minimum first sees every near point as outside; the negative key
+// of an inside point then replaces it, with ties going to the lower index.
+template <class FPC, bool DIST, bool MASKED>
+__device__ __forceinline__ void poly_rows(const float2 *__restrict__ pts, const uint8_t *__restrict__ mask, int N,
+                                          const FPC &fpc, float tx, float ty, float cs, float sn, int pbeg,
+                                          int pend, float *__restrict__ drow, int vec_store, float &bk, int &bi) {
+    constexpr int E = fp_traits<FPC>::size;
+    __shared__ int q_idx[kBlock / 32][kNearQ];
+    __shared__ float q_m[kBlock / 32][kNearQ];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int *qi = q_idx[warp];
+    float *qm = q_m[warp];
+    int qn = 0;   // queued entries (warp-uniform)
+    const float lim = fmaf(fpc.brad, 1e-5f, fpc.brad) + 1e-5f;
+    const float lim2 = lim * lim;
+
+    auto parity_pass = [&](int cnt) {   // queue entries [0, cnt), cnt <= 64
+        __syncwarp();
+        const int e0 = 2 * lane;
+        if (e0 < cnt) {
+            const bool g1 = e0 + 1 < cnt;
+            const int ia = qi[e0], ib = g1 ? qi[e0 + 1] : ia;
+            const float2 oa = __ldg(pts + ia), ob = __ldg(pts + ib);
+            float pxa, pya, pxb, pyb;
+            body_frame(oa.x, oa.y, tx, ty, cs, sn, pxa, pya);
+            body_frame(ob.x, ob.y, tx, ty, cs, sn, pxb, pyb);
+            float ma, mb;
+            unsigned sa, sb;
+            poly_eval2<E, kSign>(fpc, pxa, pya, pxb, pyb, ma, mb, sa, sb);
+            auto inside = [&](int i, float m, unsigned sg) {
+                if (sg & 0x80000000u) {
+                    const float k = __uint_as_float(__float_as_uint(m) | 0x80000000u);
+                    if (DIST) __stcs(drow + i, key_to_dist(fpc, k));
+                    if (k < bk || (k == bk && i < bi)) { bk = k; bi = i; }
+                }
+            };
+            inside(ia, qm[e0], sa);
+            if (g1) inside(ib, qm[e0 + 1], sb);
+        }
+        __syncwarp();
+    };
+
+    for (int j0 = pbeg + (int)(threadIdx.x & ~31u); j0 < pend; j0 += kBlock) {   // warp-uniform trip count
+        const int j = j0 + lane, i0 = 2 * j, i1 = 2 * j + 1;
+        bool f0 = false, f1 = false;
+        float m0 = 0.f, m1 = 0.f;
+        if (j < pend) {
+            const bool has1 = i1 < N;
+            const float2 o0 = __ldg(pts + i0);
+            const float2 o1 = has1 ? __ldg(pts + i1) : o0;
+            float px0, py0, px1, py1;
+            body_frame(o0.x, o0.y, tx, ty, cs, sn, px0, py0);
+            body_frame(o1.x, o1.y, tx, ty, cs, sn, px1, py1);
+            unsigned s0, s1;
+            poly_eval2<E, kDist>(fpc, px0, py0, px1, py1, m0, m1, s0, s1);
+            bool v0 = true, v1 = has1;
+            if (MASKED) {
+                v0 = __ldg(mask + i0) != 0;
+                v1 = has1 && __ldg(mask + i1) != 0;
+            }
+            const float k0 = v0 ? m0 : finf(), k1 = v1 ? m1 : finf();
+            const float cx0 = px0 - fpc.bcx, cy0 = py0 - fpc.bcy, cx1 = px1 - fpc.bcx, cy1 = py1 - fpc.bcy;
+            f0 = v0 && fmaf(cx0, cx0, cy0 * cy0) <= lim2;
+            f1 = v1 && fmaf(cx1, cx1, cy1 * cy1) <= lim2;
+            if (DIST) {
+                const float d0 = key_to_dist(fpc, k0);
+                const float d1 = key_to_dist(fpc, k1);
+                if (vec_store) {
+                    __stcs(reinterpret_cast<float2 *>(drow) + j, make_float2(d0, d1));
+                } else {
+                    __stcs(drow + i0, d0);
+                    if (has1) __stcs(drow + i1, d1);
+                }
+            }
+            // strict "<" keeps the lowest index among equal keys; +inf
+            // (padding) and NaN never replace the initial +inf
+            if (k0 < bk) { bk = k0; bi = i0; }
+            if (v1 && k1 < bk) { bk = k1; bi = i1; }
+        }
+        const unsigned b0 = __ballot_sync(0xffffffffu, f0), b1 = __ballot_sync(0xffffffffu, f1);
+        if (b0 | b1) {
+            const unsigned below = (1u << lane) - 1u;
+            const int pos = qn + __popc(b0 & below) + __popc(b1 & below);
+            if (f0) { qi[pos] = i0; qm[pos] = m0; }
+            if (f1) { qi[pos + (f0 ? 1 : 0)] = i1; qm[pos + (f0 ? 1 : 0)] = m1; }
+            qn += __popc(b0) + __popc(b1);
+            if (qn >= 64) {
+                parity_pass(64);
+                for (int e = lane; e < qn - 64; e += 32) {
+                    qi[e] = qi[64 + e];
+                    qm[e] = qm[64 + e];
+                }
+                qn -= 64;
+            }
+        }
+    }
+    if (qn > 0) parity_pass(qn);
+}
+
 template <class FPC, bool DIST, bool MASKED>
 __global__ void __launch_bounds__(kBlock)
 sdf_batch_kernel(const float2 *__restrict__ pts, const uint8_t *__restrict__ mask, int N,
@@ -31,6 +142,9 @@ sdf_batch_kernel(const float2 *__restrict__ pts, const uint8_t *__restrict__ mas
     float bk = finf();        // best key of this thread (first index wins ties)
     int bi = -1;
 
+    if constexpr (fp_traits<FPC>::kind == EXACT_FP_POLYGON) {
+        poly_rows<FPC, DIST, MASKED>(pts, mask, N, fpc, tx, ty, cs, sn, pbeg, pend, drow, vec_store, bk, bi);
+    } else {
     for (int j = pbeg + (int)threadIdx.x; j < pend; j += kBlock) {
         const int i0 = 2 * j, i1 = 2 * j + 1;
         const bool has1 = i1 < N;
@@ -62,6 +176,7 @@ sdf_batch_kernel(const float2 *__restrict__ pts, const uint8_t *__restrict__ mas
         // and NaN never replace the initial +inf
         if (k0 < bk) { bk = k0; bi = i0; }
         if (v1 && k1 < bk) { bk = k1; bi = i1; }
+    }
     }
 
     if (!dmin && !argmin) return;
