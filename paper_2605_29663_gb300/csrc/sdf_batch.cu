@@ -142,7 +142,9 @@ sdf_batch_kernel(const float2 *__restrict__ pts, const uint8_t *__restrict__ mas
     float bk = finf();        // best key of this thread (first index wins ties)
     int bi = -1;
 
-    if constexpr (fp_traits<FPC>::kind == EXACT_FP_POLYGON) {
+    // polygons of 8 edges or more: parity only for near points (poly_rows);
+    // below that the queue costs about what it saves
+    if constexpr (fp_traits<FPC>::kind == EXACT_FP_POLYGON && fp_traits<FPC>::size >= 8) {
         poly_rows<FPC, DIST, MASKED>(pts, mask, N, fpc, tx, ty, cs, sn, pbeg, pend, drow, vec_store, bk, bi);
     } else {
     for (int j = pbeg + (int)threadIdx.x; j < pend; j += kBlock) {
