@@ -56,7 +56,8 @@ batched_sample_kernel(const SceneDev *__restrict__ scenes, const int2 *__restric
             fp_scene = it.x;
         }
         const SmemEval ev{s_fp, D.kind, D.nfp, D.bc};
-        sample_body(D.V, ev, it.y, 0, sm, s_pts, it.x == pts_scene, pairs_per_lane, D.circ);
+        sample_body(D.V, ev, item_sample(it), 0, sm, s_pts, it.x == pts_scene, pairs_per_lane, D.circ,
+                    item_second(it));
         pts_scene = D.V.N <= kStage ? it.x : -1;
     }
 }
@@ -144,8 +145,17 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
     std::vector<int2> items, upd, val;
-    for (int s : order)
-        for (int r = 0; r < scenes[s].params.K; ++r) items.push_back(make_int2(s, r));
+    long long total_k = 0;
+    for (int s = 0; s < n_scenes; ++s) total_k += scenes[s].params.K;
+    const int sms_now = current_sm_count();
+    for (int s : order) {
+        const exact_mppi_params &p = scenes[s].params;
+        // pairs of samples per item when the whole batch has enough samples
+        // to fill the GPU at half the items (and this scene's horizon fits)
+        const bool two = pair_samples((int)std::min<long long>(total_k, 1 << 29), p.T, 1, sms_now);
+        for (int r = 0; r < p.K; r += two ? 2 : 1)
+            items.push_back(make_int2(s, r | (two && r + 1 < p.K ? kItemPair : 0)));
+    }
     for (int s = 0; s < n_scenes; ++s) {
         const exact_mppi_params &p = scenes[s].params;
         for (int q = 0; q < upd_blocks_for(p.K, p.T, p.n_u); ++q) upd.push_back(make_int2(s, q));

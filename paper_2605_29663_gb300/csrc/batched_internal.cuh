@@ -20,6 +20,12 @@ struct SceneDev {
     float4 fpc[kFpSlots];
 };
 
+// A sample item is (scene, r); bit 30 of r marks an item that also takes
+// sample r + 1 of the same scene (see sample_body).
+constexpr int kItemPair = 1 << 30;
+__device__ __forceinline__ int item_sample(int2 it) { return it.y & (kItemPair - 1); }
+__device__ __forceinline__ int item_second(int2 it) { return (it.y & kItemPair) ? (it.y & (kItemPair - 1)) + 1 : -1; }
+
 __device__ __forceinline__ void load_fp(float4 *dst, const SceneDev &D) {
     const int nf = D.kind == EXACT_FP_POLYGON ? poly_slot_count(D.nfp) : D.nfp;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) dst[i] = D.fpc[i];

@@ -27,7 +27,8 @@ batched_sample_kernel_c(const SceneDev *__restrict__ scenes, const int2 *__restr
         if (item >= n_items) break;
         const int2 it = items[item];
         const SceneDev &D = scenes[it.x];
-        sample_body(D.V, ev, it.y, 0, sm, s_pts, it.x == pts_scene, pairs_per_lane, D.circ);
+        sample_body(D.V, ev, item_sample(it), 0, sm, s_pts, it.x == pts_scene, pairs_per_lane, D.circ,
+                    item_second(it));
         pts_scene = D.V.N <= kStage ? it.x : -1;
     }
 }

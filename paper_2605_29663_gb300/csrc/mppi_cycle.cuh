@@ -105,6 +105,13 @@ inline int val_chunks_for(int N) {
 
 // Blocks per sample: split the horizon when there are too few samples to
 // fill the GPU (about `target` blocks), at most 8 parts and one step each.
+// Two samples per sample block (see sample_body) when the scene has enough
+// samples to fill the GPU at half the blocks (K >= 4 per SM) and both
+// horizons fit the block's step slots; never with a split horizon.
+inline int pair_samples(int K, int T, int parts, int sms) {
+    return parts == 1 && 2 * T <= EXACT_MAX_HORIZON && K >= 4 * (sms > 0 ? sms : 148) ? 1 : 0;
+}
+
 inline int parts_for(int K, int T, int target) {
     if (K >= target) return 1;
     int p = (target + K - 1) / K;
@@ -725,7 +732,7 @@ struct SampleSmem {
     float4 pose[EXACT_MAX_HORIZON];
     float stage[EXACT_MAX_HORIZON];
     unsigned key[EXACT_MAX_HORIZON];
-    float term;
+    float term[2];
     bool last;
 };
 
@@ -741,42 +748,54 @@ struct SampleSmem {
 // circ: bounding circles of the 64-point sub-chunks of an ordered cloud
 // (cloud_circles), or NULL.  (Kept out of SceneView: a larger SceneView
 // parameter block made the compiler spill in the large-footprint kernels.)
+// r2 >= 0: the block takes a second sample r2 of the same scene (parts == 1,
+// 2T <= EXACT_MAX_HORIZON, blockDim >= 96): warps 0 and 1 roll the two out
+// side by side, the per-step slots hold sample r's steps then r2's (slot
+// s T + h), one pass over the staged points serves both, and warps 0 and 1
+// form the two J~.  Each sample's J~ takes exactly the operations of the
+// one-sample path.
 template <bool MOVING = false, class EV>
 __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, int r, int p, SampleSmem &sm,
                                             float2 *s_pts, bool staged, int pairs_per_lane,
-                                            const float4 *circ = nullptr) {
+                                            const float4 *circ = nullptr, int r2 = -1) {
     const MppiP &P = V.P;
     const int T = P.T, nu = P.nu, N = V.N;
     constexpr int kS = stage_points_of<MOVING>();
+    const int ns = r2 >= 0 ? 2 : 1;   // samples in this block
     const int h0 = (p * T) / V.parts, h1 = ((p + 1) * T) / V.parts;
-    for (int h = h0 + (int)threadIdx.x; h < h1; h += blockDim.x) sm.key[h] = f2ord(finf());
+    const int k0 = ns == 2 ? 0 : h0, nk = ns == 2 ? 2 * T : h1 - h0;   // step slots [k0, k0 + nk)
+    for (int h = k0 + (int)threadIdx.x; h < k0 + nk; h += blockDim.x) sm.key[h] = f2ord(finf());
     const int n0 = min(N, kS);
     const float3 bc = ev.bound();
-    if (threadIdx.x < 32) {
+    const int warp = threadIdx.x >> 5;
+    if (warp < ns) {
+        const int rs = warp == 0 ? r : r2, off = warp * T;
         const float *U = V.U;
-        const float *eps = V.noise + (size_t)r * T * nu;
+        const float *eps = V.noise + (size_t)rs * T * nu;
         LaneRollout R;
         warp_rollout(P, V.state[0], V.state[1], V.state[2],
                      [&](int h, int j) { return clamp_u(P, j, U[h * nu + j] + eps[h * nu + j]); }, R);
-        const int lane = threadIdx.x;
+        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int e = 0; e < kMaxPerLane; ++e) {
             const int h = lane * R.per + e;
             if (e < R.per && h < T) {
                 float sn, cs;
                 sincosf(R.th[e], &sn, &cs);
-                sm.pose[h] = make_float4(R.x[e], R.y[e], cs, sn);
-                sm.cw[h] = make_float4(fmaf(cs, bc.x, fmaf(-sn, bc.y, R.x[e])), fmaf(sn, bc.x, fmaf(cs, bc.y, R.y[e])),
-                                       (float)(h + P.state_offset) * P.dt, 0.f);
+                sm.pose[off + h] = make_float4(R.x[e], R.y[e], cs, sn);
+                sm.cw[off + h] = make_float4(fmaf(cs, bc.x, fmaf(-sn, bc.y, R.x[e])),
+                                             fmaf(sn, bc.x, fmaf(cs, bc.y, R.y[e])),
+                                             (float)(h + P.state_offset) * P.dt, 0.f);
                 const float u2 = fmaf(R.u[e][0], R.u[e][0], fmaf(R.u[e][1], R.u[e][1], R.u[e][2] * R.u[e][2]));
-                sm.stage[h] = fmaf(P.w_goal, guidance_dist(R.x[e], R.y[e], V.wp, V.W), P.w_ctrl * u2);
+                sm.stage[off + h] = fmaf(P.w_goal, guidance_dist(R.x[e], R.y[e], V.wp, V.W), P.w_ctrl * u2);
             }
         }
-        if (lane == 0) sm.term = P.w_term * guidance_dist(R.qTx, R.qTy, V.wp, V.W);
+        if (lane == 0) sm.term[warp] = P.w_term * guidance_dist(R.qTx, R.qTy, V.wp, V.W);
         grid_dep_wait();   // launched early behind a cloud-ordering kernel: the cloud is ready now
     } else {
         grid_dep_wait();
-        if (!staged) stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, 0, n0, threadIdx.x - 32, blockDim.x - 32);
+        if (!staged)
+            stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, 0, n0, threadIdx.x - 32 * ns, blockDim.x - 32 * ns);
     }
     __syncthreads();
     const bool prune = !V.dmin && N >= kPruneMin;
@@ -793,8 +812,8 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     // without a d_min output the costs only need min(d_min, d_safe); clouds
     // of fewer than kPruneMin points are not worth the pruning phases
     const float cap = V.dmin || N < kPruneMin ? -1.f : fmaxf(P.d_safe, 0.f);
-    steps_min_keys<MOVING>(ev, s_pts, n0, sm.pose, sm.cw, h0, h1 - h0, sm.key, pairs_per_lane, sm.circ, cap,
-                           sm.msk, sm.pre);
+    steps_min_keys<MOVING>(ev, s_pts, n0, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
+                           sm.pre);
     for (int base = kS; base < N; base += kS) {   // clouds larger than the stage
         const int n = min(kS, N - base);
         __syncthreads();
@@ -807,8 +826,8 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
                 chunk_circles<MOVING>(s_pts, n, sm.circ, pairs_per_lane);
             __syncthreads();
         }
-        steps_min_keys<MOVING>(ev, s_pts, n, sm.pose, sm.cw, h0, h1 - h0, sm.key, pairs_per_lane, sm.circ, cap,
-                               sm.msk, sm.pre);
+        steps_min_keys<MOVING>(ev, s_pts, n, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
+                               sm.pre);
     }
     grid_dep_release();
     __syncthreads();
@@ -824,25 +843,26 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
             if (h < h0 || h >= h1) sm.key[h] = __ldcg(V.dkey + (size_t)r * T + h);
         __syncthreads();
     }
-    if (threadIdx.x < 32) {
+    if (warp < ns) {
+        const int rs = warp == 0 ? r : r2, off = warp * T, lane = threadIdx.x & 31;
         double acc = 0.0;
         bool unsafe = false;
-        for (int h = threadIdx.x; h < T; h += 32) {
-            const float key = ord2f(sm.key[h]);
+        for (int h = lane; h < T; h += 32) {
+            const float key = ord2f(sm.key[off + h]);
             const float d = key == finf() ? finf() : ev.dist(key);
-            if (V.dmin) V.dmin[(size_t)r * T + h] = d;
-            acc += (double)sm.stage[h] + phi_obs_d(P, d);
+            if (V.dmin) V.dmin[(size_t)rs * T + h] = d;
+            acc += (double)sm.stage[off + h] + phi_obs_d(P, d);
             unsafe |= d < P.d_safe;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         const bool chi = __any_sync(0xffffffffu, unsafe);
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             // J~ = J + w_inf I(chi) in double (Sec. IV-E); beta = min J~ is
             // gathered with one 64-bit atomic per sample into the scene's
             // header (complemented key; 0 = empty)
-            const double jt = acc + (double)sm.term + (chi ? (double)P.w_inf : 0.0);
-            V.Jt[r] = jt;
+            const double jt = acc + (double)sm.term[warp] + (chi ? (double)P.w_inf : 0.0);
+            V.Jt[rs] = jt;
             atomicMax(&V.hdr->beta_enc, ~d2ord(jt));
         }
     }

@@ -16,7 +16,7 @@ namespace exact {
 
 template <class FPC, bool MOVING, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB)
-mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev, const float4 *circ) {
+mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev, const float4 *circ, int pair) {
     extern __shared__ float2 s_pts[];   // min(N, stage) staged points (float4 each when MOVING)
     __shared__ SampleSmem sm;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -25,7 +25,14 @@ mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev, const float4 *cir
         V.hdr->ticket[1] = 0u;
         V.hdr->bad = 0;
     }
-    sample_body<MOVING>(V, ev, blockIdx.x / V.parts, blockIdx.x % V.parts, sm, s_pts, false, 1, circ);
+    // pair: block b takes samples 2b and 2b + 1; else sample b / parts,
+    // horizon part b % parts.  Only the register-capped instantiations carry
+    // the two-sample path: in the uncapped ones (large polygons) it cost the
+    // compiler spills.
+    const bool two = MINB != 0 && pair;
+    const int r = two ? 2 * (int)blockIdx.x : (int)blockIdx.x / V.parts;
+    const int p = two ? 0 : (int)blockIdx.x % V.parts;
+    sample_body<MOVING>(V, ev, r, p, sm, s_pts, false, 1, circ, two && r + 1 < V.P.K ? r + 1 : -1);
 }
 
 template <bool MOVING>
@@ -68,15 +75,19 @@ template <bool MOVING, int MINB>
 int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl = false,
                    const float4 *circ = nullptr) {
     const size_t smem = (size_t)min(V.N, stage_points_of<MOVING>()) * (MOVING ? sizeof(float4) : sizeof(float2));
+    static thread_local int sms = 0;
+    if (sms <= 0) sms = current_sm_count();
+    const int pair = MINB != 0 ? pair_samples(V.P.K, V.P.T, V.parts, sms) : 0;
+    const int grid = pair ? (V.P.K + 1) / 2 : V.P.K * V.parts;
     return with_footprint(fp, [&](auto fpc) -> int {
         using FPC = decltype(fpc);
         const ConstEval<FPC> ev{fpc};
         if (pdl) {
-            if (launch_dependent(mppi_sample_kernel<FPC, MOVING, MINB>, V.P.K * V.parts, kBlock, smem, st, V, ev, circ) !=
+            if (launch_dependent(mppi_sample_kernel<FPC, MOVING, MINB>, grid, kBlock, smem, st, V, ev, circ, pair) !=
                 cudaSuccess)
                 return EXACT_ECUDA;
         } else {
-            mppi_sample_kernel<FPC, MOVING, MINB><<<V.P.K * V.parts, kBlock, smem, st>>>(V, ev, circ);
+            mppi_sample_kernel<FPC, MOVING, MINB><<<grid, kBlock, smem, st>>>(V, ev, circ, pair);
             if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
         }
         if (launch_dependent(mppi_update_kernel<MOVING>, V.upd_blocks, kUpdBlock, 0, st, V) != cudaSuccess)
