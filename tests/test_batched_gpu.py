@@ -40,10 +40,10 @@ def _dev_scene(ex, s):
                 fp=ex.Footprint(s["kind"], s["fp"]), params=s["params"])
 
 
-def _run_batched(ex, scenes, tiles=None):
+def _run_batched(ex, scenes, tiles=None, dmin=True):
     import torch
     dev = [_dev_scene(ex, s) for s in scenes]
-    b = ex.Batch(dev, dmin=True)
+    b = ex.Batch(dev, dmin=dmin)
     if tiles:
         b.set_tiles(*tiles)
     b.step()
@@ -57,11 +57,11 @@ def _run_batched(ex, scenes, tiles=None):
     return res
 
 
-def _run_single(ex, ctx, s):
+def _run_single(ex, ctx, s, dmin=True):
     import torch
     d = _dev_scene(ex, s)
     out = ex.mppi_step(ctx, d["state"], d["cloud"], d["waypoints"], d["U"], d["noise"], d["fp"], s["params"],
-                       mask=d["mask"], dmin=True)
+                       mask=d["mask"], dmin=dmin)
     torch.cuda.synchronize()
     r = {k: v.cpu().numpy() for k, v in out.items()}
     r["U"] = d["U"].cpu().numpy()
@@ -206,3 +206,32 @@ def test_batched_ordered_clouds_change_no_cost(ex):
     for i in range(len(scenes)):
         for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
             np.testing.assert_array_equal(res[0][i][k], res[1][i][k], err_msg=f"scene {i} {k}")
+
+
+@pytest.mark.parametrize("shared_fp", [False, True])
+@pytest.mark.parametrize("dmin", [True, False])
+def test_paired_items_equal_single_scene_bitwise(ex, shared_fp, dmin):
+    """A batch of at least 4 samples per SM takes two samples of a scene per
+    item (odd K: a lone last sample; T = 64, the longest horizon that pairs;
+    T = 65 does not pair).  Each scene alone has fewer samples and runs one
+    per block, and still gives the same bits."""
+    import torch
+    if not dmin and not shared_fp:
+        pytest.skip("covered by the pruning tests")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    g = synth.rng(123)
+    scenes = []
+    for i, (K, T) in enumerate([(2 * sms + 1, 64), (sms + 1, 20), (sms + 3, 65)]):
+        s = synth.random_scene(g, [synth.DIFF, synth.ACKERMANN, synth.OMNI][i], 10, int(g.integers(400, 2500)), K, T,
+                               n_obst=20)
+        if shared_fp:
+            s["kind"], s["fp"] = synth.POLYGON, synth.l_footprint()
+        scenes.append(s)
+    got = _run_batched(ex, scenes, dmin=dmin)
+    ctx = ex.Context()
+    for i, s in enumerate(scenes):
+        ref = _run_single(ex, ctx, s, dmin=dmin)
+        for key in ("dmin", "costs", "weights", "U_upd", "U", "u_star"):
+            if key in ref:
+                np.testing.assert_array_equal(got[i][key], ref[key], err_msg=f"scene {i} {key}")
+        assert got[i]["valid"] == ref["valid"]

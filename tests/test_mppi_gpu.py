@@ -313,3 +313,29 @@ def test_cloud_order_changes_nothing(ex, ctx, masked):
     for k in ("costs", "weights", "U_upd", "U", "u_star"):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
         np.testing.assert_array_equal(b[k], c[k], err_msg=k)
+
+
+def _sm_count():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("kind", ["rects", "polygon"])
+def test_two_samples_per_block(ex, ctx, kind):
+    """K >= 4 blocks per SM with a small footprint: the register-capped
+    sample kernel takes two samples per block.  An odd K leaves the last
+    block one sample; T = 64 is the longest horizon that pairs."""
+    K = 4 * _sm_count() + 1
+
+    def make(seed):
+        s = synth.forklift(seed, K=K, T=64, N=1200)
+        if kind == "polygon":
+            s["kind"], s["fp"] = synth.POLYGON, synth.l_footprint()
+        return s
+    s, o = _seeded(make, 70)
+    compare(s, run_gpu(ex, ctx, s), o)
+    # without a d_min output (pruned path) the costs are the same bits
+    a = run_gpu(ex, ctx, s, dmin=True)
+    b = run_gpu(ex, ctx, s, dmin=False)
+    for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
