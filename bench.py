@@ -534,6 +534,55 @@ def batched_extra(torch, ex, dev, steps=3, tune=True):
             "timing": "events over consecutive steps (no graph); same scenes, same GPU"}
 
 
+def batched_small_extra(torch, ex, dev, n_scenes=128, steps=5):
+    """Many small scenes (K = 256, T = 20, N = 512, star polygons of 4-16
+    vertices, diff / Ackermann / omni): one batched step against the same
+    scenes as consecutive single-scene mppi_step calls; here the per-call
+    launches dominate and the persistent launch pays."""
+    import synth
+    g = synth.rng(5)
+    scenes = [synth.random_scene(g, [synth.DIFF, synth.ACKERMANN, synth.OMNI][i % 3], int(g.integers(4, 17)), 512,
+                                 256, 20) for i in range(n_scenes)]
+    devs = [dict(state=torch.from_numpy(s["q0"]).to(dev), cloud=torch.from_numpy(s["cloud"]).to(dev),
+                 waypoints=torch.from_numpy(s["waypoints"]).to(dev), U=torch.from_numpy(s["U"]).to(dev),
+                 noise=torch.from_numpy(s["eps"]).to(dev),
+                 mask=None if s["mask"] is None else torch.from_numpy(s["mask"]).to(dev),
+                 fp=ex.Footprint(s["kind"], s["fp"]), params=s["params"]) for s in scenes]
+    b = ex.Batch(devs)
+    b.autotune(iters=1)
+    b.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        b.step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / steps
+    ctx = ex.Context()
+    ctx.reserve(0, 256, 20, 512)
+    outs = [dict() for _ in devs]
+
+    def singles():
+        for d, o in zip(devs, outs):
+            o.update(ex.mppi_step(ctx, d["state"], d["cloud"], d["waypoints"], d["U"], d["noise"], d["fp"],
+                                  d["params"], mask=d["mask"], out=o))
+
+    singles()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        singles()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1) / steps
+    return {"scenes": n_scenes, "K": 256, "T": 20, "N": 512, "edges": "4-16",
+            "batched_ms_per_step": ms_b, "batched_scene_steps_per_s": n_scenes * 1e3 / ms_b,
+            "single_launches_ms_per_step": ms_s, "single_scene_steps_per_s": n_scenes * 1e3 / ms_s,
+            "speedup_vs_single_launches": ms_s / ms_b, "tiles": list(b.tiles),
+            "timing": "events over consecutive steps (no graph); same scenes, same GPU"}
+
+
 def run_mppi_workload(args):
     """Time one MPPI cycle workload on its own, as plain launches (for
     profiling): plain_step, forklift, predicted (the dynamic scene through
@@ -739,6 +788,7 @@ def run_gpu(args):
     if not args.no_extra and world == 1:
         line["extra"] = mppi_extra(torch, ex, dev, cpu=not args.no_cpu)
         line["extra"]["batched64"] = batched_extra(torch, ex, dev)
+        line["extra"]["batched_small128"] = batched_small_extra(torch, ex, dev)
         line["extra"]["hybrid3"] = hybrid_extra(torch, ex, dev, cpu=not args.no_cpu)
         line["extra"]["predicted"] = predicted_extra(torch, ex, dev, cpu=not args.no_cpu)
         line["extra"].update(sdf_extra(torch, ex, dev))

@@ -26,10 +26,10 @@ mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev, const float4 *cir
         V.hdr->bad = 0;
     }
     // pair: block b takes samples 2b and 2b + 1; else sample b / parts,
-    // horizon part b % parts.  Only the register-capped instantiations carry
-    // the two-sample path: in the uncapped ones (large polygons) it cost the
-    // compiler spills.
-    const bool two = MINB != 0 && pair;
+    // horizon part b % parts.  Only the register-capped static instantiations
+    // carry the two-sample path: in the uncapped ones (large polygons) it cost
+    // the compiler spills, and predicted clouds measured slower with it.
+    const bool two = MINB != 0 && !MOVING && pair;
     const int r = two ? 2 * (int)blockIdx.x : (int)blockIdx.x / V.parts;
     const int p = two ? 0 : (int)blockIdx.x % V.parts;
     sample_body<MOVING>(V, ev, r, p, sm, s_pts, false, 1, circ, two && r + 1 < V.P.K ? r + 1 : -1);
@@ -77,7 +77,7 @@ int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t s
     const size_t smem = (size_t)min(V.N, stage_points_of<MOVING>()) * (MOVING ? sizeof(float4) : sizeof(float2));
     static thread_local int sms = 0;
     if (sms <= 0) sms = current_sm_count();
-    const int pair = MINB != 0 ? pair_samples(V.P.K, V.P.T, V.parts, sms) : 0;
+    const int pair = MINB != 0 && !MOVING ? pair_samples(V.P.K, V.P.T, V.parts, sms) : 0;
     const int grid = pair ? (V.P.K + 1) / 2 : V.P.K * V.parts;
     return with_footprint(fp, [&](auto fpc) -> int {
         using FPC = decltype(fpc);
