@@ -43,6 +43,7 @@ struct PolyC {
 // Rectangle cover (Sec. IV-B.1) padded to R boxes by repeating box 0.
 template <int R>
 struct RectC {
+    f2x ncx[R], ncy[R];     // -c pairs
     float cx[R], cy[R], sx[R], sy[R];
     float bcx, bcy, brad;   // bounding circle: centre, radius (rounded up)
 };
@@ -188,40 +189,43 @@ __device__ __forceinline__ void poly_eval2(const PolyC<E> &P, float px0, float p
 // as a + |a| = 2 max(a, 0) (an add with an absolute-value operand, exact),
 // so the evaluator tracks 4 |max(a,0)|^2 and halves the root at the end:
 // both scalings by powers of two are exact.
+// Box J for two points, one per f32x2 lane (the differences and the squared
+// norm packed, the absolute values per lane: f32x2 has no absolute-value
+// form): 4 |max(a,0)|^2 in n*, max(a_x, a_y) in m*.
 template <int R, int J>
-__device__ __forceinline__ void rect_box(const RectC<R> &Q, float px, float py, float &n4, float &mx2) {
-    const float ax = fabsf(px - Q.cx[J]) - Q.sx[J];
-    const float ay = fabsf(py - Q.cy[J]) - Q.sy[J];
-    const float ux = ax + fabsf(ax), uy = ay + fabsf(ay);
-    n4 = fmaf(uy, uy, ux * ux);
-    mx2 = fmaxf(ax, ay);
+__device__ __forceinline__ void rect_box2(const RectC<R> &Q, f2x PX, f2x PY, float &n0, float &n1, float &m0,
+                                          float &m1) {
+    float dx0, dx1, dy0, dy1;
+    unpack2(add2(PX, Q.ncx[J]), dx0, dx1);
+    unpack2(add2(PY, Q.ncy[J]), dy0, dy1);
+    const float ax0 = fabsf(dx0) - Q.sx[J], ay0 = fabsf(dy0) - Q.sy[J];
+    const float ax1 = fabsf(dx1) - Q.sx[J], ay1 = fabsf(dy1) - Q.sy[J];
+    const f2x UX = pack2(ax0 + fabsf(ax0), ax1 + fabsf(ax1)), UY = pack2(ay0 + fabsf(ay0), ay1 + fabsf(ay1));
+    unpack2(fma2(UY, UY, mul2(UX, UX)), n0, n1);
+    m0 = fmaxf(ax0, ay0);
+    m1 = fmaxf(ax1, ay1);
 }
 
+// All boxes, folded into n = min_j 4 |max(a_j, 0)|^2 and
+// inner = min_j max(a_jx, a_jy) with three-input minima.
 template <int R, int J>
-__device__ __forceinline__ void rect_boxes(const RectC<R> &Q, float px, float py, float &nn, float &in) {
+__device__ __forceinline__ void rect_boxes2(const RectC<R> &Q, f2x PX, f2x PY, float &nn0, float &nn1, float &in0,
+                                            float &in1) {
     if constexpr (J + 1 < R) {
-        float na, ia, nb, ib;
-        rect_box<R, J>(Q, px, py, na, ia);
-        rect_box<R, J + 1>(Q, px, py, nb, ib);
-        nn = fmin3(nn, na, nb);
-        in = fmin3(in, ia, ib);
-        rect_boxes<R, J + 2>(Q, px, py, nn, in);
+        float na0, na1, ia0, ia1, nb0, nb1, ib0, ib1;
+        rect_box2<R, J>(Q, PX, PY, na0, na1, ia0, ia1);
+        rect_box2<R, J + 1>(Q, PX, PY, nb0, nb1, ib0, ib1);
+        nn0 = fmin3(nn0, na0, nb0); nn1 = fmin3(nn1, na1, nb1);
+        in0 = fmin3(in0, ia0, ib0); in1 = fmin3(in1, ia1, ib1);
+        rect_boxes2<R, J + 2>(Q, PX, PY, nn0, nn1, in0, in1);
     } else if constexpr (J < R) {
-        float na, ia;
-        rect_box<R, J>(Q, px, py, na, ia);
-        nn = fminf(nn, na);
-        in = fminf(in, ia);
+        float na0, na1, ia0, ia1;
+        rect_box2<R, J>(Q, PX, PY, na0, na1, ia0, ia1);
+        nn0 = fminf(nn0, na0); nn1 = fminf(nn1, na1);
+        in0 = fminf(in0, ia0); in1 = fminf(in1, ia1);
     }
 }
 
-// n4 = min_j 4 |max(a_j, 0)|^2, inner = min_j max(a_jx, a_jy).
-template <int R>
-__device__ __forceinline__ void rect_eval(const RectC<R> &Q, float px, float py, float &n4, float &inner) {
-    float nn = finf(), in = finf();
-    rect_boxes<R, 0>(Q, px, py, nn, in);
-    n4 = nn;
-    inner = in;
-}
 // Mixed key: the (negative) depth inside, 4 x the squared distance outside.
 __device__ __forceinline__ float rect_key(float n4, float inner) { return inner < 0.f ? inner : n4; }
 __device__ __forceinline__ float rect_key_to_dist(float key) { return key < 0.f ? key : 0.5f * sqrtf(key); }
@@ -279,9 +283,8 @@ __device__ __forceinline__ void eval2(const PolyC<E> &P, float px0, float py0, f
 template <int R>
 __device__ __forceinline__ void eval2(const RectC<R> &Q, float px0, float py0, float px1, float py1,
                                       float &k0, float &k1) {
-    float n0, i0, n1, i1;
-    rect_eval(Q, px0, py0, n0, i0);
-    rect_eval(Q, px1, py1, n1, i1);
+    float n0 = finf(), n1 = finf(), i0 = finf(), i1 = finf();
+    rect_boxes2<R, 0>(Q, pack2(px0, px1), pack2(py0, py1), n0, n1, i0, i1);
     k0 = rect_key(n0, i0);
     k1 = rect_key(n1, i1);
 }

@@ -76,6 +76,10 @@ inline RectC<R> make_rect(const exact_footprint *fp) {
     RectC<R> Q;
     for (int j = 0; j < R; ++j) {
         Q.cx[j] = fp->cx[j]; Q.cy[j] = fp->cy[j]; Q.sx[j] = fp->sx[j]; Q.sy[j] = fp->sy[j];
+        uint32_t ux, uy;
+        const float mx = -fp->cx[j], my = -fp->cy[j];
+        memcpy(&ux, &mx, 4); memcpy(&uy, &my, 4);
+        Q.ncx[j] = ((unsigned long long)ux << 32) | ux; Q.ncy[j] = ((unsigned long long)uy << 32) | uy;
     }
     Q.bcx = fp->bcx; Q.bcy = fp->bcy; Q.brad = fp->brad;
     return Q;
