@@ -969,12 +969,27 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
     const int K = P.K, T = P.T, nu = P.nu, TN = T * nu, G = V.upd_blocks;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nblocks = T * V.val_chunks, self = h * V.val_chunks + c;
+    // the nominal U and the start state stay unchanged until this kernel's
+    // last block: read them while the update phase drains
+    for (int e = tid; e < TN; e += kBlock) sm.U[e] = V.U[e];
     grid_dep_wait();   // the partial slots come from the update phase
 
-    // partial slots: warp w adds slots w, w + 8, ... for every element (and Z)
+    // partial slots: warp w adds slots w, w + 8, ... for every element (and
+    // Z), in that order, with four loads in flight
     for (int e = lane; e <= TN; e += 32) {
+        const float *src = V.part + e;
+        const size_t st = (size_t)kRedSlices * (TN + 1);
         float a = 0.f;
-        for (int q = warp; q < G; q += kRedSlices) a += __ldcg(V.part + (size_t)q * (TN + 1) + e);
+        int q = warp;
+        for (; q + 3 * kRedSlices < G; q += 4 * kRedSlices) {
+            const float *b = src + (size_t)q * (TN + 1);
+            const float x0 = __ldcg(b), x1 = __ldcg(b + st), x2 = __ldcg(b + 2 * st), x3 = __ldcg(b + 3 * st);
+            a += x0;
+            a += x1;
+            a += x2;
+            a += x3;
+        }
+        for (; q < G; q += kRedSlices) a += __ldcg(src + (size_t)q * (TN + 1));
         sm.red[warp][e] = a;
     }
     __syncthreads();
@@ -988,7 +1003,7 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
     for (int e = tid; e < TN; e += kBlock) {
         float a = 0.f;
         for (int w = 0; w < kRedSlices; ++w) a += sm.red[w][e];
-        const float v = V.U[e] + a * invZ;
+        const float v = sm.U[e] + a * invZ;
         sm.U[e] = v;
         if (self == 0 && V.U_upd_out) V.U_upd_out[e] = v;
     }
