@@ -160,9 +160,17 @@ __device__ __forceinline__ double ord2d(unsigned long long u) {
 template <class FPC>
 struct ConstEval {            // footprint constants in the kernel parameters
     static constexpr bool kQuad = false;   // no loads to share: two points per call
+    // small footprints: the unpruned loop gives each lane two pairs per
+    // iteration (two independent chains; larger footprints would not fit
+    // the registers)
+    static constexpr bool kPairLoop = fp_traits<FPC>::kind == EXACT_FP_RECTS || fp_traits<FPC>::size <= 6;
     FPC f;
     __device__ __forceinline__ void eval2(float px0, float py0, float px1, float py1, float &k0, float &k1) const {
         exact::eval2(f, px0, py0, px1, py1, k0, k1);
+    }
+    __device__ __forceinline__ void eval4(const float (&px)[4], const float (&py)[4], float (&k)[4]) const {
+        exact::eval2(f, px[0], py[0], px[1], py[1], k[0], k[1]);
+        exact::eval2(f, px[2], py[2], px[3], py[3], k[2], k[3]);
     }
     __device__ __forceinline__ float dist(float key) const { return key_to_dist(f, key); }
     __device__ __forceinline__ float3 bound() const { return make_float3(f.bcx, f.bcy, f.brad); }
@@ -180,6 +188,7 @@ __host__ __device__ constexpr int poly_slot_count(int E) { return 3 * E + 1 + (E
 
 struct SmemEval {
     static constexpr bool kQuad = true;   // eval4 shares each constant load among four points
+    static constexpr bool kPairLoop = true;
     const float4 *C;
     int kind, n;
     float3 bc;    // bounding circle of the footprint (centre, radius)
@@ -511,7 +520,7 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
             const float th = cw[h].z;
             float best = finf();
             const int jend = min(npairs, (c + 1) * span);
-            if constexpr (EV::kQuad) {
+            if constexpr (EV::kPairLoop) {
                 for (int j = c * span + lane; j < jend; j += 64) {
                     const bool two = j + 32 < jend;
                     float px[4], py[4], k[4];
