@@ -232,3 +232,29 @@ def test_rect_cover_vs_polygon_on_rectilinear_bodies(ex, shape):
     ins = dp <= -BAND
     assert np.all(dr[ins] >= dp[ins] - 2 * TOL)
     assert ins.sum() > 1000
+
+
+@pytest.mark.parametrize("masked", [False, True])
+def test_near_points_fill_the_parity_queue(ex, masked):
+    """Polygons of 8 edges or more take the crossing parity only for points
+    within the footprint's bounding circle, queued per warp and taken 64 at a
+    time.  Here nearly every point is near (a cloud around the footprint,
+    poses close to the origin), so the queue fills and drains on every
+    iteration; an odd N, masked points, several blocks per pose and the
+    minimum-only call are covered.  Distances match the oracle, and the
+    minimum-only call gives the bits of the full-matrix call."""
+    g = np.random.default_rng(21)
+    fp = synth.star_polygon(g, 32, 0.3, 1.2)
+    N = 20001
+    r = 1.4 * np.sqrt(g.random(N))
+    a = g.uniform(-math.pi, math.pi, N)
+    pts = np.stack([r * np.cos(a), r * np.sin(a)], axis=1).astype(np.float32)
+    mask = (g.random(N) > 0.2).astype(np.uint8) if masked else None
+    poses = _poses(g, 6, 0.2)
+    ctx = ex.Context()
+    dg, mg, ag = run_gpu(ex, pts, poses, synth.POLYGON, fp, mask=mask, ctx=ctx)
+    check(pts, poses, synth.POLYGON, fp, dg, mg, ag, mask=mask)
+    assert (dg < 0).sum() > 10000          # many inside points took the parity pass
+    _, mg2, ag2 = run_gpu(ex, pts, poses, synth.POLYGON, fp, mask=mask, ctx=ctx, dist=False)
+    np.testing.assert_array_equal(mg2, mg)
+    np.testing.assert_array_equal(ag2, ag)
