@@ -3,7 +3,9 @@
 //
 // Plan (exact_batch_create, host, once): a device scene table (parameters,
 // pointers, footprint constants, scratch addresses), the work-item list of
-// the sample phase -- one item per (scene, sample), scenes ordered by
+// the sample phase -- one item per (scene, sample), or per (scene, two
+// consecutive samples) when the batch holds at least four samples per SM and
+// the scene's horizon fits two in a block's step slots; scenes ordered by
 // per-sample cost T * N * edges, heaviest first (longest-processing-time
 // order) -- and the block tables of the update and validation phases.
 //

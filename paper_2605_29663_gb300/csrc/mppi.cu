@@ -6,7 +6,9 @@
 //                         (step, point) signed distance that can matter
 //                         (far point sub-chunks skipped), then J~; when K
 //                         is small each sample's horizon is split over
-//                         several blocks (parts) to fill the GPU.
+//                         several blocks (parts) to fill the GPU, and when
+//                         K is large the register-capped kernels give each
+//                         block two samples (K / 2 blocks).
 //   mppi_update_kernel    ceil(K / chunk) blocks (update_body): weights and
 //                         weighted clipped noise into per-block partial slots.
 //   mppi_validate_kernel  T x ceil(N / 2048) blocks (validate_body): each adds
