@@ -191,8 +191,8 @@ __device__ __forceinline__ void poly_eval2(const PolyC<E> &P, float px0, float p
 // both scalings by powers of two are exact.
 // Box J for two points, one per f32x2 lane (the differences and the squared
 // norm packed, the absolute values per lane: f32x2 has no absolute-value
-// form): 4 |max(a,0)|^2 in n*, max(a_x, a_y) in m*.
-template <int R, int J>
+// form).  PART kDist: 4 |max(a,0)|^2 in n*; kSign: max(a_x, a_y) in m*.
+template <int R, int J, int PART>
 __device__ __forceinline__ void rect_box2(const RectC<R> &Q, f2x PX, f2x PY, float &n0, float &n1, float &m0,
                                           float &m1) {
     float dx0, dx1, dy0, dy1;
@@ -200,29 +200,33 @@ __device__ __forceinline__ void rect_box2(const RectC<R> &Q, f2x PX, f2x PY, flo
     unpack2(add2(PY, Q.ncy[J]), dy0, dy1);
     const float ax0 = fabsf(dx0) - Q.sx[J], ay0 = fabsf(dy0) - Q.sy[J];
     const float ax1 = fabsf(dx1) - Q.sx[J], ay1 = fabsf(dy1) - Q.sy[J];
-    const f2x UX = pack2(ax0 + fabsf(ax0), ax1 + fabsf(ax1)), UY = pack2(ay0 + fabsf(ay0), ay1 + fabsf(ay1));
-    unpack2(fma2(UY, UY, mul2(UX, UX)), n0, n1);
-    m0 = fmaxf(ax0, ay0);
-    m1 = fmaxf(ax1, ay1);
+    if constexpr (PART & kDist) {
+        const f2x UX = pack2(ax0 + fabsf(ax0), ax1 + fabsf(ax1)), UY = pack2(ay0 + fabsf(ay0), ay1 + fabsf(ay1));
+        unpack2(fma2(UY, UY, mul2(UX, UX)), n0, n1);
+    }
+    if constexpr (PART & kSign) {
+        m0 = fmaxf(ax0, ay0);
+        m1 = fmaxf(ax1, ay1);
+    }
 }
 
-// All boxes, folded into n = min_j 4 |max(a_j, 0)|^2 and
-// inner = min_j max(a_jx, a_jy) with three-input minima.
-template <int R, int J>
+// All boxes, folded with three-input minima into n = min_j 4 |max(a_j,0)|^2
+// (kDist) and inner = min_j max(a_jx, a_jy) (kSign).
+template <int R, int J, int PART>
 __device__ __forceinline__ void rect_boxes2(const RectC<R> &Q, f2x PX, f2x PY, float &nn0, float &nn1, float &in0,
                                             float &in1) {
     if constexpr (J + 1 < R) {
         float na0, na1, ia0, ia1, nb0, nb1, ib0, ib1;
-        rect_box2<R, J>(Q, PX, PY, na0, na1, ia0, ia1);
-        rect_box2<R, J + 1>(Q, PX, PY, nb0, nb1, ib0, ib1);
-        nn0 = fmin3(nn0, na0, nb0); nn1 = fmin3(nn1, na1, nb1);
-        in0 = fmin3(in0, ia0, ib0); in1 = fmin3(in1, ia1, ib1);
-        rect_boxes2<R, J + 2>(Q, PX, PY, nn0, nn1, in0, in1);
+        rect_box2<R, J, PART>(Q, PX, PY, na0, na1, ia0, ia1);
+        rect_box2<R, J + 1, PART>(Q, PX, PY, nb0, nb1, ib0, ib1);
+        if constexpr (PART & kDist) { nn0 = fmin3(nn0, na0, nb0); nn1 = fmin3(nn1, na1, nb1); }
+        if constexpr (PART & kSign) { in0 = fmin3(in0, ia0, ib0); in1 = fmin3(in1, ia1, ib1); }
+        rect_boxes2<R, J + 2, PART>(Q, PX, PY, nn0, nn1, in0, in1);
     } else if constexpr (J < R) {
         float na0, na1, ia0, ia1;
-        rect_box2<R, J>(Q, PX, PY, na0, na1, ia0, ia1);
-        nn0 = fminf(nn0, na0); nn1 = fminf(nn1, na1);
-        in0 = fminf(in0, ia0); in1 = fminf(in1, ia1);
+        rect_box2<R, J, PART>(Q, PX, PY, na0, na1, ia0, ia1);
+        if constexpr (PART & kDist) { nn0 = fminf(nn0, na0); nn1 = fminf(nn1, na1); }
+        if constexpr (PART & kSign) { in0 = fminf(in0, ia0); in1 = fminf(in1, ia1); }
     }
 }
 
@@ -284,9 +288,28 @@ template <int R>
 __device__ __forceinline__ void eval2(const RectC<R> &Q, float px0, float py0, float px1, float py1,
                                       float &k0, float &k1) {
     float n0 = finf(), n1 = finf(), i0 = finf(), i1 = finf();
-    rect_boxes2<R, 0>(Q, pack2(px0, px1), pack2(py0, py1), n0, n1, i0, i1);
+    rect_boxes2<R, 0, kDist | kSign>(Q, pack2(px0, px1), pack2(py0, py1), n0, n1, i0, i1);
     k0 = rect_key(n0, i0);
     k1 = rect_key(n1, i1);
+}
+// The same keys with the depth pass taken only where it can decide: for a
+// point in (or on) some box the outside norm n is 0 (NaN for a non-finite
+// point); elsewhere every box has max(a_x, a_y) > 0 and the key is n.  Pays
+// where the ALU pipe is the bound (the MPPI sample phase), not in the full
+// matrix, where the extra branch costs more than the depth terms.
+template <int R>
+__device__ __forceinline__ void eval2_lazy_depth(const RectC<R> &Q, float px0, float py0, float px1, float py1,
+                                                 float &k0, float &k1) {
+    const f2x PX = pack2(px0, px1), PY = pack2(py0, py1);
+    float n0 = finf(), n1 = finf(), i0 = finf(), i1 = finf();
+    rect_boxes2<R, 0, kDist>(Q, PX, PY, n0, n1, i0, i1);
+    k0 = n0;
+    k1 = n1;
+    if (!(n0 > 0.f) || !(n1 > 0.f)) {
+        rect_boxes2<R, 0, kSign>(Q, PX, PY, n0, n1, i0, i1);
+        k0 = rect_key(n0, i0);
+        k1 = rect_key(n1, i1);
+    }
 }
 // Signed squared distance key -> signed distance (sign bit carried over).
 template <int E>

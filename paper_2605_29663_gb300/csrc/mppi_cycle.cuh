@@ -166,11 +166,14 @@ struct ConstEval {            // footprint constants in the kernel parameters
     static constexpr bool kPairLoop = fp_traits<FPC>::kind == EXACT_FP_RECTS || fp_traits<FPC>::size <= 6;
     FPC f;
     __device__ __forceinline__ void eval2(float px0, float py0, float px1, float py1, float &k0, float &k1) const {
-        exact::eval2(f, px0, py0, px1, py1, k0, k1);
+        if constexpr (fp_traits<FPC>::kind == EXACT_FP_RECTS)
+            eval2_lazy_depth(f, px0, py0, px1, py1, k0, k1);
+        else
+            exact::eval2(f, px0, py0, px1, py1, k0, k1);
     }
     __device__ __forceinline__ void eval4(const float (&px)[4], const float (&py)[4], float (&k)[4]) const {
-        exact::eval2(f, px[0], py[0], px[1], py[1], k[0], k[1]);
-        exact::eval2(f, px[2], py[2], px[3], py[3], k[2], k[3]);
+        eval2(px[0], py[0], px[1], py[1], k[0], k[1]);
+        eval2(px[2], py[2], px[3], py[3], k[2], k[3]);
     }
     __device__ __forceinline__ float dist(float key) const { return key_to_dist(f, key); }
     __device__ __forceinline__ float3 bound() const { return make_float3(f.bcx, f.bcy, f.brad); }
