@@ -348,6 +348,7 @@ __device__ __forceinline__ void chunk_circles(const float2 *pts, int n, float4 *
 // it (minima over points are exact whatever the order).
 constexpr int kSortCells = 64 * 64;
 constexpr int kSortThreads = 1024;
+constexpr int kSortRegs = 4;   // points per thread kept in registers (clouds of up to 4,096)
 struct SortSmem {
     int cnt[kSortCells + 1];
     float red[4][kSortThreads / 32];
@@ -371,10 +372,29 @@ __device__ __forceinline__ void sort_cloud_block(const float2 *__restrict__ pts,
         p = pts[i];
         return (!mask || mask[i]) && isfinite(p.x) && isfinite(p.y);
     };
+    // clouds of up to kSortRegs points per thread are read once and kept in
+    // registers (point tid + k nt in slot k); larger ones are re-read per pass
+    const bool inreg = N <= kSortRegs * nt;
+    float2 rp[kSortRegs];
+    bool rv[kSortRegs];
+    if (inreg) {
+#pragma unroll
+        for (int k = 0; k < kSortRegs; ++k) {
+            const int i = tid + k * nt;
+            rv[k] = i < N && valid(i, rp[k]);
+        }
+    }
     float lx = finf(), ly = finf(), hx = -finf(), hy = -finf();
-    for (int i = tid; i < N; i += nt) {
-        float2 p;
-        if (valid(i, p)) { lx = fminf(lx, p.x); hx = fmaxf(hx, p.x); ly = fminf(ly, p.y); hy = fmaxf(hy, p.y); }
+    auto grow = [&](float2 p) { lx = fminf(lx, p.x); hx = fmaxf(hx, p.x); ly = fminf(ly, p.y); hy = fmaxf(hy, p.y); };
+    if (inreg) {
+#pragma unroll
+        for (int k = 0; k < kSortRegs; ++k)
+            if (rv[k]) grow(rp[k]);
+    } else {
+        for (int i = tid; i < N; i += nt) {
+            float2 p;
+            if (valid(i, p)) grow(p);
+        }
     }
     lx = warp_min_f(lx); ly = warp_min_f(ly); hx = -warp_min_f(-hx); hy = -warp_min_f(-hy);
     if (lane == 0) { sm.red[0][warp] = lx; sm.red[1][warp] = ly; sm.red[2][warp] = hx; sm.red[3][warp] = hy; }
@@ -386,14 +406,24 @@ __device__ __forceinline__ void sort_cloud_block(const float2 *__restrict__ pts,
         hx = fmaxf(hx, sm.red[2][w]); hy = fmaxf(hy, sm.red[3][w]);
     }
     const float sx = 64.f / fmaxf(hx - lx, 1e-6f), sy = 64.f / fmaxf(hy - ly, 1e-6f);
-    auto cell = [&](int i, float2 &p) -> int {
-        if (!valid(i, p)) return kSortCells;
+    auto cell_of = [&](bool ok, float2 p) -> int {
+        if (!ok) return kSortCells;
         const int qx = min(63, max(0, (int)((p.x - lx) * sx))), qy = min(63, max(0, (int)((p.y - ly) * sy)));
         return (int)morton6((unsigned)qx, (unsigned)qy);
     };
-    for (int i = tid; i < N; i += nt) {
-        float2 p;
-        atomicAdd(&sm.cnt[cell(i, p)], 1);
+    int rc[kSortRegs];
+    if (inreg) {
+#pragma unroll
+        for (int k = 0; k < kSortRegs; ++k) {
+            rc[k] = cell_of(rv[k], rp[k]);
+            if (tid + k * nt < N) atomicAdd(&sm.cnt[rc[k]], 1);
+        }
+    } else {
+        for (int i = tid; i < N; i += nt) {
+            float2 p;
+            const bool ok = valid(i, p);
+            atomicAdd(&sm.cnt[cell_of(ok, p)], 1);
+        }
     }
     __syncthreads();
     // exclusive prefix over the kSortCells + 1 counts: contiguous segments per thread
@@ -418,12 +448,23 @@ __device__ __forceinline__ void sort_cloud_block(const float2 *__restrict__ pts,
     }
     __syncthreads();
     const float qnan = __int_as_float(0x7fffffff);
-    for (int i = tid; i < N; i += nt) {
-        float2 p;
-        const int c = cell(i, p);
+    auto place = [&](int i, int c, float2 p) {
         const int pos = atomicAdd(&sm.cnt[c], 1);
         opts[pos] = c < kSortCells ? p : make_float2(qnan, qnan);
         if (MOVING) ovel[pos] = c < kSortCells ? vel[i] : make_float2(0.f, 0.f);
+    };
+    if (inreg) {
+#pragma unroll
+        for (int k = 0; k < kSortRegs; ++k) {
+            const int i = tid + k * nt;
+            if (i < N) place(i, rc[k], rp[k]);
+        }
+    } else {
+        for (int i = tid; i < N; i += nt) {
+            float2 p;
+            const bool ok = valid(i, p);
+            place(i, cell_of(ok, p), p);
+        }
     }
 }
 
