@@ -299,11 +299,15 @@ extern "C" int mppi_step_batched(exact_batch *b, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     int rc = launch_sample(b, b->d_scenes, st);
     if (rc != EXACT_OK) return rc;
-    batched_update_kernel<<<b->n_upd, kUpdBlock, 0, st>>>(b->d_scenes, b->d_upd);
-    if (!b->uniform) {
-        batched_validate_kernel<<<b->n_val, kBlock, 0, st>>>(b->d_scenes, b->d_val);
-        return cuda_status(cudaGetLastError());
-    }
+    // update and validation start while their predecessor drains
+    // (programmatic dependent launch; the bodies wait where they read its
+    // results, as in the single-scene cycle)
+    if (launch_dependent(batched_update_kernel, (unsigned)b->n_upd, (unsigned)kUpdBlock, 0, st,
+                         (const SceneDev *)b->d_scenes, (const int2 *)b->d_upd) != cudaSuccess)
+        return EXACT_ECUDA;
+    if (!b->uniform)
+        return cuda_status(launch_dependent(batched_validate_kernel, (unsigned)b->n_val, (unsigned)kBlock, 0, st,
+                                            (const SceneDev *)b->d_scenes, (const int2 *)b->d_val));
     return b->fp.kind == EXACT_FP_POLYGON && b->fp.n_pad > 16 ? launch_uniform_large(b, b->d_scenes, st, true)
                                                                : launch_uniform_small(b, b->d_scenes, st, true);
 }

@@ -64,8 +64,8 @@ int launch_uniform_sample_t(exact_batch *b, const SceneDev *table, cudaStream_t 
 
 template <class FPC>
 int launch_uniform_validate_t(exact_batch *b, cudaStream_t st, const FPC &fpc) {
-    batched_validate_kernel_c<FPC><<<b->n_val, kBlock, 0, st>>>(b->d_scenes, b->d_val, ConstEval<FPC>{fpc});
-    return cuda_status(cudaGetLastError());
+    return cuda_status(launch_dependent(batched_validate_kernel_c<FPC>, (unsigned)b->n_val, (unsigned)kBlock, 0, st,
+                                        (const SceneDev *)b->d_scenes, (const int2 *)b->d_val, ConstEval<FPC>{fpc}));
 }
 
 // Per size class (returns EXACT_EINVAL for a footprint of the other class).

@@ -8,7 +8,7 @@
 // Everything stays on the device, so a whole hybrid cycle is capturable.
 #include <new>
 
-#include "internal.h"
+#include "mppi_cycle.cuh"
 
 namespace exact {
 
@@ -24,6 +24,7 @@ struct HybridTable {
 
 __global__ void hybrid_select_kernel(const HybridTable t, int *__restrict__ state, float *__restrict__ u_out,
                                      float *__restrict__ Jbar) {
+    grid_dep_wait();   // launched behind the validation phase: its results are ready now
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     const int m_prev = state[0], tau = state[1];
     int best = -1;
@@ -114,6 +115,6 @@ extern "C" int mppi_step_hybrid(exact_hybrid *h, int *mode_state, float *u_out, 
     cudaStream_t st = (cudaStream_t)stream;
     const int rc = mppi_step_batched(h->batch, stream);
     if (rc != EXACT_OK) return rc;
-    hybrid_select_kernel<<<1, 32, 0, st>>>(h->tab, mode_state, u_out, Jbar);
-    return cuda_status(cudaGetLastError());
+    return cuda_status(launch_dependent(hybrid_select_kernel, 1u, 32u, 0, st, (const HybridTable)h->tab, mode_state,
+                                        u_out, Jbar));
 }

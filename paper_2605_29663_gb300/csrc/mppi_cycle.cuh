@@ -1026,6 +1026,7 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
     // last block: read them while the update phase drains
     for (int e = tid; e < TN; e += kBlock) sm.U[e] = V.U[e];
     grid_dep_wait();   // the partial slots come from the update phase
+    grid_dep_release();   // a dependent launch (the hybrid selection) waits for this grid's end anyway
 
     // partial slots: warp w adds slots w, w + 8, ... for every element (and
     // Z), in that order, with four loads in flight
