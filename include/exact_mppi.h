@@ -291,7 +291,9 @@ typedef struct {
 } exact_scene;
 
 /* A batch plan: validates the scenes, uploads a device scene table, the
- * work-item list (one item per (scene, sample), heaviest first) and the
+ * work-item list (one item per (scene, sample), or per two samples of a
+ * scene when the batch holds at least four samples per SM and T <= 64;
+ * heaviest scenes first) and the
  * per-scene scratch (synchronous; allocates device memory).  The scene
  * pointers are fixed for the life of the plan; their contents may change
  * between steps.  1 <= n_scenes <= 4096; each scene obeys the mppi_step
