@@ -401,7 +401,7 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--episodes", type=int, default=100)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--out", default="gpurun_out/learned.json")
+    ap.add_argument("--out", default="learned.json")
     a = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
