@@ -45,9 +45,9 @@ L2_BYTES = 129 * 1024 * 1024
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the headline kernel, from the ncu capture summarised in
-# profiles/sdf_batch_kernel_poly32_16384x8192.md, valid only while the kernel
-# sources hash to the recorded value (reported as null otherwise).
+# the headline kernel, taken from one ncu capture of the headline workload and
+# valid only while the kernel sources hash to the recorded value (reported as
+# null otherwise).
 TRAFFIC = {"sources": ["paper_2605_29663_gb300/csrc/sdf_batch.cu", "paper_2605_29663_gb300/csrc/common.cuh",
                        "paper_2605_29663_gb300/csrc/internal.h"],
            "sha256_16": "d71e18adb593d732", "bytes_per_launch": 406784 + 478232576}

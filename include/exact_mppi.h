@@ -165,7 +165,7 @@ int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint
               float *dmin, void *stream);
 
 /* mppi_step with time-indexed obstacle predictions (the extension named in
- * Sec. VI: signed-distance costs against predicted obstacle positions along
+ * Sec. V-F: signed-distance costs against predicted obstacle positions along
  * the horizon instead of the current observation only).  Every point i has a
  * velocity v_i and at horizon step h it is evaluated at the constant-velocity
  * prediction o_i + t_h v_i, t_h = (h + state_offset) dt being the time of the
@@ -324,7 +324,7 @@ int exact_batch_get_tiles(const exact_batch *batch, int *threads, int *pairs_per
 int exact_batch_set_tiles(exact_batch *batch, int threads, int pairs_per_lane);
 
 /* ------------------------------------------------------------------ hybrid modes
- * Hybrid-mode EXACT-MPPI (Sec. III-F, Algorithm 2, steps 1-2) for platforms
+ * Hybrid-mode EXACT-MPPI (Sec. IV-F, Algorithm 2, steps 1-2) for platforms
  * with several non-skidding motion modes (e.g. Ackermann, parallel, spin).
  * Each mode m is a scene (exact_scene) of the same robot: it shares the
  * caller's state, cloud and footprint as the caller chooses and has its own

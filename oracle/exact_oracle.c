@@ -272,7 +272,7 @@ static int near_threshold(double d, double d_safe, double tol) {
  * J plus the unsafe flag chi (Sec. IV-E).  dmin_out (T) may be NULL; *near
  * counts horizon steps whose d_min lies within tol of 0 or d_safe.
  * vel (N x 2) or NULL: time-indexed obstacle prediction (the extension of
- * Sec. VI) -- at step h the points are at o + t v, t = (h + state_offset) dt
+ * Sec. V-F) -- at step h the points are at o + t v, t = (h + state_offset) dt
  * the time of the scored state; moved (N x 2) is scratch for them. */
 static double sequence_cost(const ox_params *P, const double q0[3], const double *u,
                             const double *cloud, const double *vel, double *moved,
@@ -418,7 +418,7 @@ int ox_mppi_step(const ox_params *P, const double q0[3],
 }
 
 /* ---------------------------------------------------------------------------
- * Hybrid-mode selection (Sec. III-F, Algorithm 2, steps 1 and 2).  Every mode
+ * Hybrid-mode selection (Sec. IV-F, Algorithm 2, steps 1 and 2).  Every mode
  * m of the set has already run its own Algorithm 1 cycle, giving the cost
  * J[m] of its updated nominal and its validation flag valid[m].
  *   Jbar_m = J_m + lambda_switch * I(m != m_prev) if valid, else +inf;

@@ -1,4 +1,4 @@
-// hybrid.cu -- hybrid-mode EXACT-MPPI (Sec. III-F, Algorithm 2, steps 1-2).
+// hybrid.cu -- hybrid-mode EXACT-MPPI (Sec. IV-F, Algorithm 2, steps 1-2).
 //
 // The modes of one robot are the scenes of one batch plan: a step runs
 // Algorithm 1 for every mode in the batched launch set (persistent sample

@@ -512,7 +512,7 @@ __device__ __forceinline__ void cloud_circles(const float2 *__restrict__ pts, co
 //
 // MOVING: each staged entry is (o_x, o_y, v_x, v_y) and the point of step h
 // is the constant-velocity prediction o + t_h v at the time t_h of the scored
-// state (the time-indexed obstacle prediction of Sec. VI).
+// state (the time-indexed obstacle prediction of Sec. V-F).
 //
 // Schedule, in three block-wide phases:
 //  1. one lane per (step, sub-chunk): keep the pair unless the sub-chunk's

@@ -1,5 +1,5 @@
 // mppi_predicted.cu -- mppi_step_predicted: the control cycle of mppi_step
-// with time-indexed obstacle predictions (the extension named in Sec. VI):
+// with time-indexed obstacle predictions (the extension named in Sec. V-F):
 // every obstacle point carries a velocity and each horizon step's signed
 // distances are taken against the constant-velocity prediction o + t_h v at
 // the time t_h of the scored state, instead of the current observation only.

@@ -216,8 +216,6 @@ def test_paired_items_equal_single_scene_bitwise(ex, shared_fp, dmin):
     T = 65 does not pair).  Each scene alone has fewer samples and runs one
     per block, and still gives the same bits."""
     import torch
-    if not dmin and not shared_fp:
-        pytest.skip("covered by the pruning tests")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     g = synth.rng(123)
     scenes = []

@@ -1,4 +1,4 @@
-"""Hybrid-mode EXACT-MPPI on the GPU (Sec. III-F, Algorithm 2, steps 1-2):
+"""Hybrid-mode EXACT-MPPI on the GPU (Sec. IV-F, Algorithm 2, steps 1-2):
 the nominal cost J_m that each mode's cycle reports, and the hybrid cycle
 (all modes in one batched launch set plus the device-side selection)
 against the FP64 oracle over several consecutive cycles, the safe stop and

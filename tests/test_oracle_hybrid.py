@@ -1,4 +1,4 @@
-"""Pins of the FP64 oracle's hybrid-mode cycle (Sec. III-F, Algorithm 2,
+"""Pins of the FP64 oracle's hybrid-mode cycle (Sec. IV-F, Algorithm 2,
 steps 1-2): the nominal cost J_m that each mode's Algorithm 1 cycle reports,
 checked against closed-form positions and clearances, and the mode selection
 (switch penalty, validation exclusion, safe stop, cooldown) on hand-made

@@ -1,5 +1,5 @@
 """Pins of the FP64 oracle's time-indexed obstacle prediction (the extension
-named in Sec. VI, constant-velocity reading): each horizon step scores the
+named in Sec. V-F, constant-velocity reading): each horizon step scores the
 points at o + t_h v, t_h the time of the scored state.  Checked against closed
 forms of a box robot and a moving point, the static special case and the
 literal-indexing switch."""
