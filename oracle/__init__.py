@@ -70,6 +70,10 @@ def lib():
             _lib.ox_hybrid_select.restype = I
             _lib.ox_hybrid_select.argtypes = [I, P, P, D, I, P, P, P]
             _lib.ox_polar_hist.argtypes = [P, P, I, D, D, D, I, D, P]
+            _lib.ox_proposal_features.argtypes = [P, I, D, D, D, D, D, D, P, P, I, P]
+            _lib.ox_proposal_prepare.argtypes = [P, P, L, P, P]
+            _lib.ox_proposal_select.restype = I
+            _lib.ox_proposal_select.argtypes = [P, P, I, P, P, P, P, I, I, P, P]
             _lib.ox_mlp_forward.argtypes = [P] * 6 + [I, I, I, P, I, P]
             _lib.ox_mlp_loss_grad.restype = D
             _lib.ox_mlp_loss_grad.argtypes = [P] * 6 + [I, I, I, P, P, I] + [P] * 6
@@ -279,6 +283,43 @@ def polar_hist(points, pose, nbins: int = 64, r_max: float = 10.0, mask=None) ->
     lib().ox_polar_hist(pts.ctypes.data, None if m is None else m.ctypes.data, pts.shape[0],
                         x, y, th, nbins, r_max, out.ctypes.data)
     return out
+
+
+def proposal_features(hist, pose, goal, prev_cmd, U_prev, r_max: float = 10.0) -> np.ndarray:
+    """Network input of one robot: [hist / r_max, goal in the robot frame /
+    r_max, previous command, |goal| / r_max, cos and sin of the goal bearing,
+    previous nominal U (T x 2)]."""
+    h = _f64(hist, (-1,))
+    U = _f64(U_prev, (-1, 2))
+    pc = _f64(prev_cmd, (2,))
+    out = np.empty(h.size + 7 + 2 * U.shape[0])
+    x, y, th = (float(v) for v in pose)
+    lib().ox_proposal_features(h.ctypes.data, h.size, r_max, x, y, th, float(goal[0]), float(goal[1]),
+                               pc.ctypes.data, U.ctypes.data, U.shape[0], out.ctypes.data)
+    return out
+
+
+def proposal_prepare(U_prev, shift):
+    """(U_prev + shift, U_prev) as float64 arrays of U_prev's shape."""
+    U = _f64(U_prev)
+    sh = _f64(shift, U.shape)
+    a, b = np.empty_like(U), np.empty_like(U)
+    lib().ox_proposal_prepare(U.ctypes.data, sh.ctypes.data, U.size, a.ctypes.data, b.ctypes.data)
+    return a, b
+
+
+def proposal_select(costs_prop, costs_plain, U_prop, U_plain, u_prop, u_plain):
+    """One robot: (kept proposal?, U_out, u_out) -- the proposal candidate is
+    kept only when its best cost is strictly lower than plain MPPI's."""
+    cp, cq = _f64(costs_prop, (-1,)), _f64(costs_plain, (-1,))
+    assert cp.size == cq.size
+    Up, Uq = _f64(U_prop), _f64(U_plain, np.shape(U_prop))
+    up, uq = _f64(u_prop, (-1,)), _f64(u_plain, (-1,))
+    Uo, uo = np.empty_like(Up), np.empty_like(up)
+    pick = lib().ox_proposal_select(cp.ctypes.data, cq.ctypes.data, cp.size, Up.ctypes.data, Uq.ctypes.data,
+                                    up.ctypes.data, uq.ctypes.data, Up.size, up.size, Uo.ctypes.data,
+                                    uo.ctypes.data)
+    return bool(pick), Uo, uo
 
 
 def mlp_forward(W, x) -> np.ndarray:

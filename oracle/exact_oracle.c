@@ -468,6 +468,62 @@ void ox_polar_hist(const double *pts, const uint8_t *mask, int N, double x, doub
 }
 
 /* ---------------------------------------------------------------------------
+ * Learned-proposal network input of one robot (project feature layout; the
+ * paper has no learned component):
+ *   [hist / r_max (nbins), goal in the robot frame / r_max (2),
+ *    previous command (v, omega), |goal| / r_max, cos and sin of the goal
+ *    bearing, previous nominal U (T x 2)].
+ * The goal is moved into the robot frame as any obstacle point (Sec. IV-C.1);
+ * the bearing is atan2 of its robot-frame coordinates (0 for a goal at the
+ * robot's position).  out has nbins + 7 + 2 T entries.
+ * ------------------------------------------------------------------------- */
+void ox_proposal_features(const double *hist, int nbins, double r_max, double x, double y, double th,
+                          double goal_x, double goal_y, const double *prev_cmd, const double *U_prev, int T,
+                          double *out) {
+    for (int k = 0; k < nbins; ++k) out[k] = hist[k] / r_max;
+    double gx, gy;
+    ox_body_frame(goal_x, goal_y, x, y, th, &gx, &gy);
+    double range = sqrt(gx * gx + gy * gy);
+    double bearing = atan2(gy, gx);
+    out[nbins + 0] = gx / r_max;
+    out[nbins + 1] = gy / r_max;
+    out[nbins + 2] = prev_cmd[0];
+    out[nbins + 3] = prev_cmd[1];
+    out[nbins + 4] = range / r_max;
+    out[nbins + 5] = cos(bearing);
+    out[nbins + 6] = sin(bearing);
+    for (int k = 0; k < 2 * T; ++k) out[nbins + 7 + k] = U_prev[k];
+}
+
+/* The two candidate nominals of a proposal-guided cycle: the proposal's
+ * U_prev + shift and the plain U_prev (n entries each). */
+void ox_proposal_prepare(const double *U_prev, const double *shift, int64_t n, double *U_prop, double *U_plain) {
+    for (int64_t e = 0; e < n; ++e) {
+        U_prop[e] = U_prev[e] + shift[e];
+        U_plain[e] = U_prev[e];
+    }
+}
+
+/* Fallback rule of the proposal-guided cycle for one robot: keep the
+ * proposal candidate only when its best sample cost is strictly lower than
+ * plain MPPI's (on a tie plain MPPI is kept); copy the kept candidate's
+ * nominal (TN entries) and command (nu entries).  Returns 1 when the
+ * proposal is kept. */
+int ox_proposal_select(const double *costs_prop, const double *costs_plain, int K, const double *U_prop,
+                       const double *U_plain, const double *u_prop, const double *u_plain, int TN, int nu,
+                       double *U_out, double *u_out) {
+    double best_prop = INFINITY, best_plain = INFINITY;
+    for (int r = 0; r < K; ++r) {
+        if (costs_prop[r] < best_prop) best_prop = costs_prop[r];
+        if (costs_plain[r] < best_plain) best_plain = costs_plain[r];
+    }
+    int pick = best_prop < best_plain;
+    for (int e = 0; e < TN; ++e) U_out[e] = pick ? U_prop[e] : U_plain[e];
+    for (int j = 0; j < nu; ++j) u_out[j] = pick ? u_prop[j] : u_plain[j];
+    return pick;
+}
+
+/* ---------------------------------------------------------------------------
  * Proposal MLP: y = W3 g(W2 g(W1 x + b1) + b2) + b3 with the exact GELU
  * g(z) = z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)).  Row-major weights:
  * W1 (H x D), W2 (H x H), W3 (O x H).  Batch rows are independent.

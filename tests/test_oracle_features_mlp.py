@@ -1,7 +1,10 @@
 """Pins of the oracle's learned-proposal pieces: the polar nearest-range
 histogram, the GELU MLP forward pass (against torch's CPU fp64 ops), its
-analytic gradients (against central finite differences) and Adam (against
-the closed form of its first step)."""
+analytic gradients (against central finite differences), Adam (against the
+closed form of its first step), and the proposal-guided cycle's network input
+(hand-derived goals ahead / beside / behind the robot, rigid-motion
+invariance), candidate preparation and fallback selection (hand-made cost
+tables with ties, numpy's minimum)."""
 import math
 
 import numpy as np
@@ -83,3 +86,81 @@ def test_adam_first_step_closed_form():
     np.testing.assert_allclose(w, w0 - 1e-3 * grad / (np.abs(grad) + 1e-8), rtol=1e-14, atol=1e-16)
     np.testing.assert_allclose(m, 0.1 * grad, rtol=1e-14)
     np.testing.assert_allclose(v, 0.001 * grad ** 2, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- proposal path
+def _feat(pose, goal, T=2, hist=None, prev=(0.25, -0.5), r_max=10.0):
+    hist = np.linspace(0.5, 10.0, 64) if hist is None else hist
+    U = np.arange(2 * T, dtype=np.float64).reshape(T, 2) * 0.1
+    return oracle.proposal_features(hist, pose, goal, prev, U, r_max), hist, U
+
+
+@pytest.mark.parametrize("pose,goal,expect", [
+    # facing +y from (1, 1): a goal at (1, 4) is 3 m straight ahead
+    ((1.0, 1.0, math.pi / 2), (1.0, 4.0), (0.3, 0.0, 0.3, 1.0, 0.0)),
+    # facing +x from the origin: (0, 2) is 2 m to the left (bearing +90 deg)
+    ((0.0, 0.0, 0.0), (0.0, 2.0), (0.0, 0.2, 0.2, 0.0, 1.0)),
+    # facing -x from (2, -1): (5, -1) is 3 m behind (bearing 180 deg)
+    ((2.0, -1.0, math.pi), (5.0, -1.0), (-0.3, 0.0, 0.3, -1.0, 0.0)),
+    # facing +x: the 3-4-5 triangle
+    ((0.0, 0.0, 0.0), (3.0, 4.0), (0.3, 0.4, 0.5, 0.6, 0.8)),
+    # facing -y from (0, 0): (4, 0) is to the left (rotate the world by +90 deg)
+    ((0.0, 0.0, -math.pi / 2), (4.0, 0.0), (0.0, 0.4, 0.4, 0.0, 1.0)),
+    # goal at the robot: zero range, bearing 0
+    ((1.5, -2.0, 0.7), (1.5, -2.0), (0.0, 0.0, 0.0, 1.0, 0.0)),
+])
+def test_proposal_features_hand_values(pose, goal, expect):
+    x, hist, U = _feat(pose, goal)
+    nb = hist.size
+    assert x.shape == (nb + 7 + 4,)
+    np.testing.assert_allclose(x[:nb], hist / 10.0, rtol=0, atol=1e-15)
+    gx, gy, rng, cb, sb = expect
+    np.testing.assert_allclose(x[nb:nb + 7], [gx, gy, 0.25, -0.5, rng, cb, sb], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(x[nb + 7:], U.reshape(-1))
+
+
+def test_proposal_features_rigid_motion():
+    """Moving robot and goal by the same rigid motion leaves the features unchanged."""
+    g = np.random.default_rng(11)
+    for _ in range(20):
+        pose = (g.uniform(-3, 3), g.uniform(-3, 3), g.uniform(-math.pi, math.pi))
+        goal = (g.uniform(-8, 8), g.uniform(-8, 8))
+        a, _, _ = _feat(pose, goal)
+        phi, t = g.uniform(-math.pi, math.pi), g.uniform(-5, 5, 2)
+        c, s = math.cos(phi), math.sin(phi)
+        mv = lambda p: (c * p[0] - s * p[1] + t[0], s * p[0] + c * p[1] + t[1])
+        b, _, _ = _feat((*mv(pose[:2]), pose[2] + phi), mv(goal))
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+
+
+def test_proposal_prepare_closed_form():
+    U = np.array([[1.0, 2.0], [3.0, 4.0]])
+    shift = np.array([[0.5, -1.0], [0.0, 0.25]])
+    a, b = oracle.proposal_prepare(U, shift)
+    np.testing.assert_array_equal(a, [[1.5, 1.0], [3.0, 4.25]])
+    np.testing.assert_array_equal(b, U)
+
+
+@pytest.mark.parametrize("cp,cq,pick", [
+    ([1.0, 7.0], [2.0, 3.0], True),            # proposal's best is lower
+    ([3.0, 1.0, 5.0], [1.0, 4.0, 4.0], False),  # equal best costs: plain MPPI is kept
+    ([9.0, 9.0, 0.5], [1.0, 1.0, 1.0], True),   # decided by the last sample
+    ([4.0], [3.5], False),                      # K = 1
+    ([np.inf, np.inf], [np.inf, 2.0], False),   # nothing finite on the proposal side
+])
+def test_proposal_select_tables(cp, cq, pick):
+    Up, Uq = np.full((3, 2), 1.0), np.full((3, 2), -1.0)
+    up, uq = np.array([0.5, 0.25]), np.array([-0.5, -0.25])
+    got, Uo, uo = oracle.proposal_select(cp, cq, Up, Uq, up, uq)
+    assert got == pick
+    np.testing.assert_array_equal(Uo, Up if pick else Uq)
+    np.testing.assert_array_equal(uo, up if pick else uq)
+
+
+def test_proposal_select_random_against_numpy_minimum():
+    g = np.random.default_rng(12)
+    for _ in range(50):
+        K = int(g.integers(1, 40))
+        cp, cq = g.uniform(0, 10, K), g.uniform(0, 10, K)
+        got, _, _ = oracle.proposal_select(cp, cq, np.zeros((2, 2)), np.ones((2, 2)), np.zeros(2), np.ones(2))
+        assert got == bool(np.min(cp) < np.min(cq))
