@@ -652,6 +652,31 @@ def run_mppi_workload(args):
     return 0
 
 
+def mppi_summary(extra: dict) -> dict:
+    """The headline figures of the MPPI cycle measurements in `extra`."""
+    out = {}
+    for key, name in (("plain_step", "plain_K256_T20_N512"), ("forklift", "forklift_K2048_T40_N4096")):
+        e = extra.get(key)
+        if e:
+            out[name] = {"us_per_step": round(e["us_per_step"], 2), "steps_per_s": round(e["steps_per_s"], 1)}
+    h = extra.get("hybrid3")
+    if h:
+        out["hybrid_3modes_K1024"] = {"us_per_cycle": round(h["us_per_cycle"], 2),
+                                      "cycles_per_s": round(h["cycles_per_s"], 1)}
+    p = extra.get("predicted")
+    if p:
+        out["predicted_K1024_T20_N2048"] = {"us_per_step": round(p["predicted_us_per_step"], 2),
+                                            "static_us_per_step": round(p["static_us_per_step"], 2)}
+    for key in ("batched64", "batched_small128"):
+        b = extra.get(key)
+        if b:
+            out[key] = {"batched_ms_per_step": round(b["batched_ms_per_step"], 3),
+                        "single_launches_ms_per_step": round(b["single_launches_ms_per_step"], 3),
+                        "speedup_vs_single_launches": round(b["speedup_vs_single_launches"], 3),
+                        "timing": b.get("timing", "")}
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -717,28 +742,70 @@ def run_gpu(args):
     evals = P * N_POINTS * N_VERTS
     value = whole_job_value(world, evals, ms)
 
-    # end to end through the public call with host buffers: H2D of the step's
-    # inputs from pinned memory, the call, D2H of the per-pose min / argmin
+    # end to end through the public call with host buffers, every step: the
+    # H2D copy of the step's inputs from pinned memory, the call, and the D2H
+    # copy of its whole result (the full distance matrix, min and argmin) into
+    # pinned memory.  Two device / host result buffers let the D2H copy of step
+    # i (copy stream) overlap the kernel of step i + 1; the kernel of step i + 2
+    # waits until the copy of step i has drained its buffer.
     h_pts = torch.from_numpy(w["points"]).pin_memory()
     h_poses = torch.from_numpy(w["poses"]).pin_memory()
-    h_m = torch.empty(P, dtype=torch.float32).pin_memory()
-    h_a = torch.empty(P, dtype=torch.int32).pin_memory()
     e_steps = max(3, min(args.steps, 10))
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(e_steps):
+    bufs = [out, {"dist": torch.empty_like(d), "dmin": torch.empty_like(m), "argmin": torch.empty_like(a)}]
+    hbufs = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()} for o in bufs]
+    copy_stream = torch.cuda.Stream(device=dev)
+    done = [torch.cuda.Event() for _ in bufs]
+    drained = [None, None]
+    cur = torch.cuda.current_stream(dev)
+
+    def e2e_step(i):
+        k = i % 2
+        if drained[k] is not None:
+            cur.wait_event(drained[k])
         pts.copy_(h_pts, non_blocking=True)
         poses.copy_(h_poses, non_blocking=True)
-        ex.sdf_batch(pts, poses, fp, ctx=ctx, out=out)
-        h_m.copy_(m, non_blocking=True)
-        h_a.copy_(a, non_blocking=True)
-    e1.record()
+        ex.sdf_batch(pts, poses, fp, ctx=ctx, out=bufs[k])
+        done[k].record(cur)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(done[k])
+            for key in ("dist", "dmin", "argmin"):
+                hbufs[k][key].copy_(bufs[k][key], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(copy_stream)
+            drained[k] = ev
+
+    for i in range(2):   # warm-up of the pipeline (pinned buffers touched once)
+        e2e_step(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for i in range(e_steps):
+        e2e_step(i)
+    cur.wait_stream(copy_stream)
+    e1.record(cur)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e_steps
     e2e_val = world * evals / (e2e_ms * 1e-3)
     h2d = h_pts.numel() * 4 + h_poses.numel() * 4
-    d2h = h_m.numel() * 4 + h_a.numel() * 4
+    d2h = sum(v.numel() * v.element_size() for v in hbufs[0].values())
+    ok = np.array_equal(hbufs[(e_steps - 1) % 2]["dmin"].numpy(), m.cpu().numpy())
+    del bufs[1], hbufs
+
+    # the same with the minimum-only call (no distance matrix): H2D of the
+    # inputs, the call, D2H of min + argmin, in order on one stream
+    h_m = torch.empty(P, dtype=torch.float32).pin_memory()
+    h_a = torch.empty(P, dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    e0.record(cur)
+    for _ in range(e_steps):
+        pts.copy_(h_pts, non_blocking=True)
+        poses.copy_(h_poses, non_blocking=True)
+        ex.sdf_batch(pts, poses, fp, ctx=ctx, dist=False, out=out)
+        h_m.copy_(m, non_blocking=True)
+        h_a.copy_(a, non_blocking=True)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    mo_ms = e0.elapsed_time(e1) / e_steps
 
     if rank != 0:
         if dist is not None:
@@ -777,9 +844,14 @@ def run_gpu(args):
                      "peak_basis": f"152 SMs x 128 FP32 lanes x 2 (FMA) x {sm_max:.0f} MHz max SM clock "
                                    "(derived; MEASURED_PEAKS.json carries only HBM and bf16 figures)"},
         "e2e": {"value": e2e_val, "unit": "point-edge evals/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h,
-                "note": "pinned H2D of points+poses, exact_sdf_batch, D2H of per-pose min+argmin; "
-                        "the full distance matrix stays in HBM"},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e_steps, "result_check": bool(ok),
+                "note": "every step: pinned H2D of points + poses, exact_sdf_batch, D2H of the whole result "
+                        "(full distance matrix + min + argmin) into pinned memory on a copy stream; two result "
+                        "buffers let a step's D2H overlap the next step's kernel"},
+        "e2e_min_only": {"value": world * evals / (mo_ms * 1e-3), "unit": "point-edge evals/s",
+                         "ms_per_step": mo_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": P * 8,
+                         "note": "the minimum-only call (no distance matrix): pinned H2D of points + poses, "
+                                 "exact_sdf_batch(dist=NULL), D2H of min + argmin, in order on one stream"},
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
@@ -792,6 +864,7 @@ def run_gpu(args):
         line["extra"]["hybrid3"] = hybrid_extra(torch, ex, dev, cpu=not args.no_cpu)
         line["extra"]["predicted"] = predicted_extra(torch, ex, dev, cpu=not args.no_cpu)
         line["extra"].update(sdf_extra(torch, ex, dev))
+        line["mppi"] = mppi_summary(line["extra"])   # last key: short enough to survive a truncated tail
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -240,10 +240,14 @@ int exact_proposal_select(const float *costs_prop, const float *costs_plain, int
  * cudaMalloc after start-up, code running during stream capture, a program
  * whose device memory belongs to another allocator).
  *
- * mppi_step_noalloc computes exactly what mppi_step computes (same kernels,
- * same results) without a context: its scratch is a file-scope device
+ * mppi_step_noalloc computes what mppi_step computes (the same kernels, the
+ * same output bits) without a context: its scratch is a file-scope device
  * array of EXACT_NOALLOC_ARENA_BYTES that every GPU loading the library
- * holds until the process exits.  It allocates nothing (no cudaMalloc,
+ * holds until the process exits.  One difference in cost, not in results:
+ * without a d_min output and with 1,024 points or more, mppi_step prunes far
+ * point chunks on a spatially ordered copy of the cloud kept in its context,
+ * while this call prunes on the cloud in the order given, which skips fewer
+ * chunks (and so runs slower) when consecutive points are not close together.  It allocates nothing (no cudaMalloc,
  * cudaFree or allocating library call); it clears the parts of the array
  * that must start at zero with stream-ordered memsets on `stream`.
  *  - The first call on a device looks the array's device address up (once,

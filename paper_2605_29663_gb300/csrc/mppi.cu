@@ -135,7 +135,7 @@ int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const
         V.mask = nullptr;
         cc = circ;
     }
-    return launch_cycle(V, fp, st, sort, cc);
+    return launch_cycle(V, fp, st, sort, cc, ctx->sm_count > 0 ? ctx->sm_count : current_sm_count());
 }
 
 // Clouds with point velocities go to mppi_predicted.cu.  Static clouds go to
@@ -143,14 +143,13 @@ int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const
 // four blocks per SM and the footprint is small (a rectangle cover or at most
 // 16 edges: larger polygons need more registers than the cap leaves), else
 // to the unbounded ones here.
-int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ) {
-    if (V.vel) return launch_cycle_moving(V, fp, st, pdl, circ);
-    static thread_local int sms = 0;
-    if (sms <= 0) sms = current_sm_count();
+int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
+                 int sms) {
+    if (sms <= 0) sms = 148;
+    if (V.vel) return launch_cycle_moving(V, fp, st, pdl, circ, sms);
     const bool small_fp = fp->kind == EXACT_FP_RECTS || fp->n_pad <= 16;
-    if (small_fp && (long long)V.P.K * V.parts > 4LL * (sms > 0 ? sms : 148))
-        return launch_cycle_dense(V, fp, st, pdl, circ);
-    return launch_cycle_t<false, 0>(V, fp, st, pdl, circ);
+    if (small_fp && (long long)V.P.K * V.parts > 4LL * sms) return launch_cycle_dense(V, fp, st, pdl, circ, sms);
+    return launch_cycle_t<false, 0>(V, fp, st, pdl, circ, sms);
 }
 
 }  // namespace exact

@@ -72,11 +72,9 @@ inline size_t cloud_copy_bytes(int N, bool moving) {
 // pdl: the sample kernel follows a cloud-ordering kernel and may start early
 // (its rollouts do not read the cloud; sample_body waits before staging).
 template <bool MOVING, int MINB>
-int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl = false,
-                   const float4 *circ = nullptr) {
+int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
+                   int sms) {
     const size_t smem = (size_t)min(V.N, stage_points_of<MOVING>()) * (MOVING ? sizeof(float4) : sizeof(float2));
-    static thread_local int sms = 0;
-    if (sms <= 0) sms = current_sm_count();
     const int pair = MINB != 0 && !MOVING ? pair_samples(V.P.K, V.P.T, V.parts, sms) : 0;
     const int grid = pair ? (V.P.K + 1) / 2 : V.P.K * V.parts;
     return with_footprint(fp, [&](auto fpc) -> int {
@@ -100,11 +98,14 @@ int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t s
 }
 
 // Any cycle (mppi.cu: picks one of the three below), the static capped cycle
-// (mppi_dense.cu) and the predicted cycle (mppi_predicted.cu).
-int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl = false,
-                 const float4 *circ = nullptr);
-int launch_cycle_dense(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ);
-int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ);
+// (mppi_dense.cu) and the predicted cycle (mppi_predicted.cu).  sms is the
+// SM count of the device the cycle runs on (it sizes the grids).
+int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
+                 int sms);
+int launch_cycle_dense(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
+                       int sms);
+int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
+                        int sms);
 
 // mppi_step with optional point velocities (NULL: static cloud).
 int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const float *velocity,

@@ -11,8 +11,8 @@
 namespace exact {
 
 int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl,
-                        const float4 *circ) {
-    return launch_cycle_t<true, 4>(V, fp, st, pdl, circ);
+                        const float4 *circ, int sms) {
+    return launch_cycle_t<true, 4>(V, fp, st, pdl, circ, sms);
 }
 
 }  // namespace exact

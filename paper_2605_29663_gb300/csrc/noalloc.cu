@@ -15,7 +15,8 @@
 namespace exact {
 int check_params(const exact_mppi_params *p);
 MppiP to_device_params(const exact_mppi_params *p);
-int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ);
+int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
+                 int sms);
 }  // namespace exact
 
 using namespace exact;
@@ -91,5 +92,5 @@ extern "C" int mppi_step_noalloc(const float *state, const float *cloud, const u
     // and counters that must start at zero (no allocation involved)
     if (cudaMemsetAsync(arena, 0, kArenaHeader, st) != cudaSuccess) return EXACT_ECUDA;
     if (parts > 1 && cudaMemsetAsync(V.tk, 0, (size_t)P.K * sizeof(unsigned), st) != cudaSuccess) return EXACT_ECUDA;
-    return launch_cycle(V, fp, st, false, nullptr);
+    return launch_cycle(V, fp, st, false, nullptr, sms);
 }

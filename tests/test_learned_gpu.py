@@ -115,45 +115,47 @@ def torch_u8(a):
 
 
 def test_features_prepare_select(ex):
+    """The proposal kernels against the oracle's ox_proposal_features /
+    _prepare / _select on the same float32 inputs: the network input within
+    float32 rounding (2e-5 relative, 2e-6 absolute), the prepared candidates
+    and the selection (decision and copies) bit for bit."""
     import torch
     g = np.random.default_rng(6)
-    B, T, nb = 5, 20, 64
+    B, T, nb = 7, 20, 64
     hist = g.uniform(0, 10, (B, nb)).astype(np.float32)
     poses = np.column_stack([g.uniform(-2, 2, (B, 2)), g.uniform(-3, 3, B)]).astype(np.float32)
     goals = g.uniform(-8, 8, (B, 2)).astype(np.float32)
+    goals[0] = poses[0, :2]                     # goal at the robot: zero range, bearing 0
     prev = g.normal(size=(B, 2)).astype(np.float32)
     U = g.normal(size=(B, T, 2)).astype(np.float32)
     x = ex.proposal_features(_t(hist), _t(poses), _t(goals), _t(prev), _t(U), 10.0).cpu().numpy()
     assert x.shape == (B, nb + 7 + 2 * T)
-    np.testing.assert_allclose(x[:, :nb], hist / 10.0, rtol=1e-6)
-    np.testing.assert_allclose(x[:, nb + 7:], U.reshape(B, -1))
     for b in range(B):
-        _, _, _ = None, None, None
-        gb = oracle.sdf_batch([goals[b]], [poses[b]], oracle.RECTS, [[0, 0, 1e-9, 1e-9]])  # unused, keeps oracle warm
-        c, s = math.cos(poses[b, 2]), math.sin(poses[b, 2])
-        dx, dy = goals[b] - poses[b, :2]
-        gx, gy = c * dx + s * dy, -s * dx + c * dy
-        dist = math.hypot(gx, gy)
-        np.testing.assert_allclose(x[b, nb:nb + 7], [gx / 10, gy / 10, prev[b, 0], prev[b, 1], dist / 10, gx / dist,
-                                                     gy / dist], rtol=2e-5, atol=2e-6)
+        xo = oracle.proposal_features(hist[b], poses[b], goals[b], prev[b], U[b], 10.0)
+        np.testing.assert_allclose(x[b], xo, rtol=2e-5, atol=2e-6, err_msg=f"robot {b}")
     shift = g.normal(size=(B, T, 2)).astype(np.float32)
     Up, Uq = torch.empty((B, T, 2), device="cuda"), torch.empty((B, T, 2), device="cuda")
     ex.proposal_prepare(_t(U), _t(shift), Up, Uq)
-    np.testing.assert_array_equal(Up.cpu().numpy(), U + shift)
-    np.testing.assert_array_equal(Uq.cpu().numpy(), U)
+    po, qo = oracle.proposal_prepare(U, shift)
+    np.testing.assert_array_equal(Up.cpu().numpy(), po.astype(np.float32))
+    np.testing.assert_array_equal(Uq.cpu().numpy(), qo.astype(np.float32))
     K = 33
     cp = g.uniform(0, 10, (B, K)).astype(np.float32)
     cq = g.uniform(0, 10, (B, K)).astype(np.float32)
-    cq[0] = cp[0]                       # tie -> plain
+    cq[0] = cp[0]                               # equal best costs: plain MPPI is kept
+    cq[1, 5] = cp[1].min()                      # a tie through a different sample
+    cp[2, -1] = cq[2].min() - 1e-3              # decided by the last sample
     up, uq = g.normal(size=(B, 2)).astype(np.float32), g.normal(size=(B, 2)).astype(np.float32)
     Uo, uo = torch.empty((B, T, 2), device="cuda"), torch.empty((B, 2), device="cuda")
     chose = torch.empty(B, dtype=torch.int32, device="cuda")
     ex.proposal_select(_t(cp), _t(cq), Up, Uq, _t(up), _t(uq), Uo, uo, chose)
-    pick = cp.min(1) < cq.min(1)
-    np.testing.assert_array_equal(chose.cpu().numpy(), pick.astype(np.int32))
-    assert not pick[0]
-    np.testing.assert_array_equal(Uo.cpu().numpy(), np.where(pick[:, None, None], U + shift, U))
-    np.testing.assert_array_equal(uo.cpu().numpy(), np.where(pick[:, None], up, uq))
+    Upn, Uqn = Up.cpu().numpy(), Uq.cpu().numpy()
+    for b in range(B):
+        pick, Ur, ur = oracle.proposal_select(cp[b], cq[b], Upn[b], Uqn[b], up[b], uq[b])
+        assert int(chose[b].item()) == int(pick), b
+        np.testing.assert_array_equal(Uo[b].cpu().numpy(), Ur.astype(np.float32))
+        np.testing.assert_array_equal(uo[b].cpu().numpy(), ur.astype(np.float32))
+    assert not bool(chose[0].item()) and not bool(chose[1].item()) and bool(chose[2].item())
 
 
 def test_trained_proposal_gains_over_plain(ex):

@@ -182,36 +182,20 @@ def test_closed_loop_three_cycles(ex, ctx):
         torch.cuda.synchronize()
         sigma = np.array([0.3, 0.6])
         err = np.abs(Ug.cpu().numpy() - o["U"]) / np.maximum(np.abs(o["U"]), sigma)
-        assert err.max() <= 3 * REL, (cyc, err.max())
+        assert err.max() <= REL, (cyc, err.max())
         Uo = Ug.cpu().numpy().astype(np.float64)   # continue from the GPU state
 
 
-def test_full_size_forklift_sampled(ex, ctx):
-    """K=2048, T=40, N=4096, R=3 in the benchmark's launch: 8 sampled rollouts
-    re-scored by the oracle; weights = softmax of the GPU's own costs; the
-    update = the weighted clipped noise (FP64 recomputation)."""
-    s = synth.forklift(0)
-    g = run_gpu(ex, ctx, s, dmin=True)
-    p = s["params"]
-    rows = np.random.default_rng(1).choice(p["K"], 8, replace=False)
-    for r in rows:
-        s1 = dict(s, eps=s["eps"][r:r + 1], params=dict(p, K=1))
-        o1 = run_oracle(s1)
-        if o1["n_near"]:
-            continue
-        assert abs(g["costs"][r] - o1["costs"][0]) <= 1e-5 * abs(o1["costs"][0]) + 1e-3
-        assert np.max(np.abs(g["dmin"][r] - o1["dmin"][0])) <= D_TOL
-    c = g["costs"].astype(np.float64)
-    w = np.exp(-(c - c.min()) / p["lambda"])
-    w /= w.sum()
-    big = w >= 1e-6 * w.max()
-    assert np.max(np.abs(g["weights"][big] - w[big]) / w[big]) <= 1e-3   # costs are rounded to float32
-    U0 = s["U"].astype(np.float64)
-    lo, hi = np.array(p["u_min"][:2]), np.array(p["u_max"][:2])
-    epsc = np.clip(U0[None] + s["eps"], lo, hi) - U0[None]
-    upd = U0 + np.einsum("r,rtj->tj", g["weights"].astype(np.float64), epsc)
-    scale = np.maximum(np.abs(upd), np.array([0.3, 0.2]))
-    assert np.max(np.abs(g["U_upd"] - upd) / scale) <= REL
+@pytest.mark.parametrize("dmin", [True, False])
+def test_full_size_forklift(ex, ctx, dmin):
+    """K=2048, T=40, N=4096, 3-box rectangle cover, Ackermann with the steering
+    clamp -- the forklift workload in the launch the benchmark times --
+    against the oracle's Algorithm 1 cycle element by element: J~, omega,
+    U_upd, u*, the shifted U and the validation flag; with a d_min output
+    also every d_min.  Without it the cloud is put in spatial order and far
+    sub-chunks are pruned (the benchmark's configuration)."""
+    s, o = _seeded(lambda k: synth.forklift(k), 0)
+    compare(s, run_gpu(ex, ctx, s, dmin=dmin), o, check_dmin=dmin)
 
 
 def test_context_reused_across_shapes_and_entry_points(ex):
