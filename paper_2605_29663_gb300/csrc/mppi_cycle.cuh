@@ -164,6 +164,10 @@ struct ConstEval {            // footprint constants in the kernel parameters
     // iteration (two independent chains; larger footprints would not fit
     // the registers)
     static constexpr bool kPairLoop = fp_traits<FPC>::kind == EXACT_FP_RECTS || fp_traits<FPC>::size <= 6;
+    // point-level pruning of small clouds for rectangle covers and polygons
+    // of up to 16 edges (another inlined copy of the unrolled evaluator of a
+    // larger polygon costs more compile time than the pruning saves)
+    static constexpr bool kQueueOk = fp_traits<FPC>::kind == EXACT_FP_RECTS || fp_traits<FPC>::size <= 16;
     FPC f;
     __device__ __forceinline__ void eval2(float px0, float py0, float px1, float py1, float &k0, float &k1) const {
         if constexpr (fp_traits<FPC>::kind == EXACT_FP_RECTS)
@@ -192,6 +196,7 @@ __host__ __device__ constexpr int poly_slot_count(int E) { return 3 * E + 1 + (E
 struct SmemEval {
     static constexpr bool kQuad = true;   // eval4 shares each constant load among four points
     static constexpr bool kPairLoop = true;
+    static constexpr bool kQueueOk = true;
     const float4 *C;
     int kind, n;
     float3 bc;    // bounding circle of the footprint (centre, radius)
@@ -296,7 +301,8 @@ struct SmemEval {
 // speed) of its valid points (radius -1 when it has none).
 constexpr int kSub = 64;
 constexpr float kPruneSlack = 1e-3f;   // m: far above the float rounding of the distances
-constexpr int kPruneMin = 1024;        // points: smaller clouds skip the pruning phases
+constexpr int kPruneMin = 1024;        // points: smaller clouds are pruned point by point (see steps_min_keys)
+constexpr int kQueueAll = 1024;        // entries of the block's queues of kept (step, point) pairs
 
 template <bool MOVING>
 __device__ __forceinline__ void chunk_circles(const float2 *pts, int n, float4 *circ, int ppl) {
@@ -531,7 +537,8 @@ __device__ __forceinline__ void cloud_circles(const float2 *__restrict__ pts, co
 template <bool MOVING = false, class EV>
 __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose,
                                                const float4 *cw, int h0, int nh, unsigned *keyh, int ppl,
-                                               const float4 *circ, float cap, unsigned *msk, int *pre) {
+                                               const float4 *circ, float cap, unsigned *msk, int *pre,
+                                               int *queue = nullptr) {
     const int npairs = (n + 1) >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nsub = (n + kSub * ppl - 1) / (kSub * ppl);
@@ -553,7 +560,7 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
         body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
         body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
     };
-    if (cap < 0.f) {
+    if (cap < 0.f || (queue && !EV::kQueueOk)) {   // no pruning
         const int span = 32 * 4;   // pairs per item
         const int nchunk = npairs > 0 ? (npairs + span - 1) / span : 0;
         const int items = nh * nchunk;
@@ -599,6 +606,98 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
             best = warp_min_f(best);
             if (lane == 0) atomicMin(keyh + h, f2ord(best));
         }
+        return;
+    }
+    if constexpr (EV::kQueueOk) if (queue) {
+        // Point-level pruning (clouds below kPruneMin, no sort, no circles):
+        // the warp walks its contiguous share of the (step, pair) units; each
+        // lane keeps a point only if it lies within the footprint's bounding
+        // circle at that step plus cap (and the slack of the chunk test, taken
+        // for a circle of radius 0); kept (step, point) entries are appended to
+        // the warp's queue and evaluated 64 at a time, two per lane (the two
+        // lanes of the packed evaluator may hold points of different steps:
+        // the footprint is the same in every body frame), each key folded into
+        // its step's minimum with a shared atomicMin.  A warp's queue holds
+        // kQueueAll / warps entries: with 128 or more a flush waits for 64
+        // entries, with fewer every iteration that adds some flushes them.
+        const float3 bc = ev.bound();
+        const float lim = cap + kPruneSlack;
+        const int cap_q = kQueueAll / nwarps;
+        const int flush_at = cap_q >= 128 ? 64 : 1;
+        int *q = queue + warp * cap_q;
+        int qn = 0;   // warp-uniform
+        const long long units = (long long)nh * npairs;
+        const int e0 = (int)((units * warp) / nwarps), e1 = (int)((units * (warp + 1)) / nwarps);
+        auto point_at = [&](int i, int h) -> float2 {
+            if constexpr (MOVING) {
+                const float th = cw[h].z;
+                const float4 a = reinterpret_cast<const float4 *>(pts)[i];
+                return make_float2(fmaf(th, a.z, a.x), fmaf(th, a.w, a.y));
+            } else {
+                return pts[i];
+            }
+        };
+        auto flush = [&](int cnt) {   // entries [0, cnt), cnt <= 64
+            __syncwarp();
+            const int a = 2 * lane;
+            if (a < cnt) {
+                const bool two = a + 1 < cnt;
+                const int ea = q[a], eb = two ? q[a + 1] : ea;
+                const int ha = h0 + (ea >> 12), hb = h0 + (eb >> 12);
+                const float2 oa = point_at(ea & 4095, ha), ob = point_at(eb & 4095, hb);
+                const float4 pa = pose[ha], pb = pose[hb];
+                float pxa, pya, pxb, pyb;
+                body_frame(oa.x, oa.y, pa.x, pa.y, pa.z, pa.w, pxa, pya);
+                body_frame(ob.x, ob.y, pb.x, pb.y, pb.z, pb.w, pxb, pyb);
+                float ka, kb;
+                ev.eval2(pxa, pya, pxb, pyb, ka, kb);
+                atomicMin(keyh + ha, f2ord(ka));
+                if (two) atomicMin(keyh + hb, f2ord(kb));
+            }
+            __syncwarp();
+        };
+        // lane's first unit, then advance by 32 units per iteration
+        int hh = 0, j = 0;
+        if (e0 + lane < e1) {
+            hh = (e0 + lane) / npairs;
+            j = e0 + lane - hh * npairs;
+        }
+        for (int base = e0; base < e1; base += 32) {
+            bool k0 = false, k1 = false;
+            const int i0 = 2 * j, i1 = 2 * j + 1;
+            if (base + lane < e1) {
+                const float4 c = cw[h0 + hh];
+                const float reach = bc.z + lim + 1e-5f * (fabsf(c.x) + fabsf(c.y));
+                const float2 o0 = point_at(i0, h0 + hh);
+                const float dx0 = o0.x - c.x, dy0 = o0.y - c.y;
+                const float f0 = fmaf(1e-5f, fabsf(o0.x) + fabsf(o0.y), reach);
+                k0 = fmaf(dx0, dx0, dy0 * dy0) <= f0 * f0;   // NaN (masked) never kept
+                if (i1 < n) {
+                    const float2 o1 = point_at(i1, h0 + hh);
+                    const float dx1 = o1.x - c.x, dy1 = o1.y - c.y;
+                    const float f1 = fmaf(1e-5f, fabsf(o1.x) + fabsf(o1.y), reach);
+                    k1 = fmaf(dx1, dx1, dy1 * dy1) <= f1 * f1;
+                }
+            }
+            const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
+            if (b0 | b1) {
+                const unsigned below = (1u << lane) - 1u;
+                const int pos = qn + __popc(b0 & below) + __popc(b1 & below);
+                if (k0) q[pos] = (hh << 12) | i0;
+                if (k1) q[pos + (k0 ? 1 : 0)] = (hh << 12) | i1;
+                qn += __popc(b0) + __popc(b1);
+                if (qn >= flush_at) {
+                    const int f = min(qn, 64);
+                    flush(f);
+                    for (int e = lane; e < qn - f; e += 32) q[e] = q[f + e];
+                    __syncwarp();
+                    qn -= f;
+                }
+            }
+            j += 32;
+            while (j >= npairs) { j -= npairs; ++hh; }
+        }
+        if (qn > 0) flush(qn);
         return;
     }
     const float brad = ev.bound().z;
@@ -778,10 +877,15 @@ __device__ __forceinline__ double phi_obs_d(const MppiP &P, float d) {
 }
 
 struct SampleSmem {
-    float4 circ[kStage / kSub];        // sub-chunk bounding circles
+    union {
+        struct {
+            float4 circ[kStage / kSub];            // sub-chunk bounding circles
+            unsigned msk[2 * EXACT_MAX_HORIZON];   // kept (step, sub-chunk) pairs, 64 bits per step
+            int pre[EXACT_MAX_HORIZON + 1];        // exclusive prefix of their counts
+        };
+        int queue[kQueueAll];   // per-warp queues of kept (step, point) pairs (clouds below kPruneMin)
+    };
     float4 cw[EXACT_MAX_HORIZON];      // footprint circle centre (world) and t_h per step
-    unsigned msk[2 * EXACT_MAX_HORIZON];   // kept (step, sub-chunk) pairs, 64 bits per step
-    int pre[EXACT_MAX_HORIZON + 1];        // exclusive prefix of their counts
     float4 pose[EXACT_MAX_HORIZON];
     float stage[EXACT_MAX_HORIZON];
     unsigned key[EXACT_MAX_HORIZON];
@@ -862,11 +966,12 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
             chunk_circles<MOVING>(s_pts, n0, sm.circ, pairs_per_lane);
         __syncthreads();
     }
-    // without a d_min output the costs only need min(d_min, d_safe); clouds
-    // of fewer than kPruneMin points are not worth the pruning phases
-    const float cap = V.dmin || N < kPruneMin ? -1.f : fmaxf(P.d_safe, 0.f);
+    // without a d_min output the costs only need min(d_min, d_safe): far
+    // sub-chunks (clouds of kPruneMin points or more) or far points (smaller
+    // clouds, one pass) are skipped
+    const float cap = V.dmin ? -1.f : fmaxf(P.d_safe, 0.f);
     steps_min_keys<MOVING>(ev, s_pts, n0, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
-                           sm.pre);
+                           sm.pre, !V.dmin && N < kPruneMin ? sm.queue : nullptr);
     for (int base = kS; base < N; base += kS) {   // clouds larger than the stage
         const int n = min(kS, N - base);
         __syncthreads();

@@ -323,3 +323,43 @@ def test_two_samples_per_block(ex, ctx, kind):
     b = run_gpu(ex, ctx, s, dmin=False)
     for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def _small_cloud_case(seed, K, T, N, kind, masked):
+    s = synth.plain_step(seed, K=K, T=T, N=N)
+    if kind == "rects":
+        s["kind"], s["fp"] = synth.RECTS, synth.forklift_rects()
+    elif kind == "poly16":
+        s["fp"] = synth.star_polygon(synth.rng(seed), 16, 0.3, 1.2)
+    elif kind == "poly24":
+        s["fp"] = synth.star_polygon(synth.rng(seed), 24, 0.3, 1.2)
+    if masked:
+        m = (synth.rng(seed + 7).random(N) > 0.3).astype(np.uint8)
+        s["mask"] = m
+    return s
+
+
+@pytest.mark.parametrize("K,T,N,kind,masked", [
+    (256, 20, 512, "L", False),        # the plain-step workload
+    (64, 128, 1023, "L", True),        # longest horizon, largest small cloud, masked
+    (300, 7, 1, "L", False),           # a single point
+    (96, 17, 33, "rects", True),       # odd N (a lone last point), rectangle cover
+    (40, 9, 200, "poly16", False),     # split horizon (few samples), 16 edges
+    (130, 12, 300, "poly24", False),   # larger polygons are not pruned point by point
+    (700, 64, 700, "L", False),        # two samples per block (2T = 128 step slots)
+])
+def test_point_pruning_small_clouds(ex, ctx, K, T, N, kind, masked):
+    """Clouds below 1,024 points without a d_min output are pruned point by
+    point: a (step, point) pair is evaluated only when the point lies within
+    d_safe (plus a rounding slack) of the footprint's bounding circle at that
+    step.  Costs, weights and the updated sequences are the same bits as the
+    run with a d_min output (which evaluates every pair), and match the oracle."""
+    def make(seed):
+        return _small_cloud_case(seed, K, T, N, kind, masked)
+    s, o = _seeded(make, 300 + K + N)
+    a = run_gpu(ex, ctx, s, dmin=True)
+    b = run_gpu(ex, ctx, s, dmin=False)
+    for k in ("costs", "weights", "U_upd", "U", "u_star"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    assert a["valid"] == b["valid"]
+    compare(s, b, o, check_dmin=False)

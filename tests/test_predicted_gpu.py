@@ -156,3 +156,21 @@ def test_predicted_cloud_order_changes_nothing(ex, ctx):
         outs.append(dict({k: v.cpu().numpy() for k, v in out.items()}, U=U.cpu().numpy()))
     for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
         np.testing.assert_array_equal(outs[0][k], outs[1][k], err_msg=k)
+
+
+def test_small_predicted_cloud_point_pruning(ex, ctx):
+    """A predicted cloud below 1,024 points without a d_min output is pruned
+    point by point at each step's predicted positions; the same bits as the
+    run with a d_min output, and the oracle's values."""
+    import torch
+    s, o = _seeded(lambda k: synth.dynamic_scene(k, K=256, T=20, N=900), 40)
+    a = _run(ex, ctx, s)
+    fp = ex.Footprint(s["kind"], s["fp"])
+    U = _t(s["U"].astype(np.float32))
+    out = ex.mppi_step(ctx, _t(s["q0"]), _t(s["cloud"]), _t(s["waypoints"]), U, _t(s["eps"]), fp, s["params"],
+                       mask=None if s["mask"] is None else _t(s["mask"]), velocity=_t(s["vel"]), dmin=False)
+    torch.cuda.synchronize()
+    for k in ("costs", "weights", "U_upd", "u_star"):
+        np.testing.assert_array_equal(out[k].cpu().numpy(), a[k], err_msg=k)
+    np.testing.assert_array_equal(U.cpu().numpy(), a["U"])
+    compare(s, a, o)
