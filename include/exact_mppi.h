@@ -38,8 +38,9 @@ typedef enum {
     EXACT_ENOTSIMPLE = 2,   /* polygon is not simple (self-intersection, repeated vertex, zero area) */
     EXACT_ECAPACITY = 3,    /* size beyond a documented maximum */
     EXACT_ECUDA = 4,        /* a CUDA runtime call failed */
-    EXACT_ETIMEOUT = 5      /* a bounded device-side wait gave up (reserved: no kernel of this
-                               library waits on another block; phases end with atomic tickets) */
+    EXACT_ETIMEOUT = 5      /* a bounded device-side wait gave up: the bulk copy that stages a
+                               block's obstacle points did not complete (no kernel of this library
+                               waits on another block; phases end with atomic tickets) */
 } exact_status;
 
 typedef enum { EXACT_FP_POLYGON = 0, EXACT_FP_RECTS = 1 } exact_fp_kind;
@@ -95,9 +96,21 @@ int exact_ctx_reserve(exact_ctx *ctx, int max_poses, int max_K, int max_T);
  * the input order), so a step with a larger cloud than any before may
  * allocate -- reserve ahead of stream capture. */
 int exact_ctx_reserve_cloud(exact_ctx *ctx, int max_poses, int max_K, int max_T, int max_points);
-/* Device-side error word (an exact_status); synchronises the device, then
- * returns and clears it. */
-int exact_ctx_get_error(exact_ctx *ctx);
+/* Device-side error word of the context (an exact_status, 0 = none): the
+ * first error a kernel launched with this context recorded.  Kernels record
+ *   EXACT_EINVAL    non-finite device data the host cannot check: the start
+ *                   state, the nominal U or the noise of mppi_step, a pose of
+ *                   exact_sdf_batch (the call still runs; its results are
+ *                   not meaningful);
+ *   EXACT_ETIMEOUT  a staging copy that did not complete within its bounded
+ *                   wait;
+ *   EXACT_ECAPACITY an index out of range, in the debug build only
+ *                   (compiled with -DEXACT_DEBUG_CHECKS: every checked access
+ *                   is skipped instead of made).
+ * The word is read and cleared in the order of `stream` (the stream of the
+ * calls whose errors are wanted), which is then synchronised; other streams
+ * and the rest of the device are not waited for. */
+int exact_ctx_get_error(exact_ctx *ctx, void *stream);
 
 /* ------------------------------------------------------------------ SDF batch
  * Batched exact signed distance (Sec. IV-C, IV-D; the evaluator of
@@ -322,6 +335,11 @@ int mppi_step_batched(exact_batch *batch, void *stream);
  * writes the timings as JSON text (at most json_cap bytes, NUL-terminated).
  * Synchronises `stream`. */
 int exact_batch_autotune(exact_batch *batch, int iters, char *json_out, int json_cap, void *stream);
+/* The batch's device error word (as exact_ctx_get_error: first error of
+ * any of its kernels, read and cleared in the order of `stream`, which is
+ * then synchronised).  A hybrid object reports through its batch
+ * (exact_hybrid_batch). */
+int exact_batch_get_error(exact_batch *batch, void *stream);
 /* Current tile shape of the batch. */
 int exact_batch_get_tiles(const exact_batch *batch, int *threads, int *pairs_per_lane);
 /* Set the tile shape (threads in {64, 128, 256, 512}, pairs_per_lane in 1..8). */

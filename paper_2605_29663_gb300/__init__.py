@@ -30,6 +30,7 @@ EXPORTS = ["exact_status_string", "exact_footprint_create", "exact_footprint_des
            "exact_ctx_get_error", "exact_sdf_batch", "mppi_step", "mppi_step_predicted", "exact_batch_create",
            "exact_batch_destroy",
            "mppi_step_batched", "exact_batch_autotune", "exact_batch_get_tiles", "exact_batch_set_tiles",
+           "exact_batch_get_error",
            "mppi_step_noalloc", "exact_mlp_create", "exact_mlp_destroy", "exact_mlp_num_params",
            "exact_mlp_set_params", "exact_mlp_get_params", "exact_mlp_forward", "exact_mlp_loss_grad",
            "exact_mlp_train_step", "exact_polar_hist", "exact_proposal_features", "exact_proposal_prepare",
@@ -55,81 +56,103 @@ def load() -> ctypes.CDLL:
         if not os.path.exists(_build.LIB_PATH):
             raise RuntimeError(f"{_build.LIB_PATH} is missing: build it with "
                                "`python -m paper_2605_29663_gb300.build` (nvcc, sm_103a)")
-        lib = ctypes.CDLL(_build.LIB_PATH)
-        P, I, V = ctypes.c_void_p, ctypes.c_int, None
-        lib.exact_status_string.restype = ctypes.c_char_p
-        lib.exact_status_string.argtypes = [I]
-        lib.exact_footprint_create.restype = I
-        lib.exact_footprint_create.argtypes = [I, P, I, ctypes.POINTER(P)]
-        lib.exact_footprint_destroy.restype = V
-        lib.exact_footprint_destroy.argtypes = [P]
-        lib.exact_footprint_info.restype = I
-        lib.exact_footprint_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
-        lib.exact_ctx_create.restype = I
-        lib.exact_ctx_create.argtypes = [ctypes.POINTER(P)]
-        lib.exact_ctx_destroy.restype = V
-        lib.exact_ctx_destroy.argtypes = [P]
-        lib.exact_ctx_reserve.restype = I
-        lib.exact_ctx_reserve.argtypes = [P, I, I, I]
-        lib.exact_ctx_reserve_cloud.restype = I
-        lib.exact_ctx_reserve_cloud.argtypes = [P, I, I, I, I]
-        lib.exact_ctx_get_error.restype = I
-        lib.exact_ctx_get_error.argtypes = [P]
-        lib.exact_sdf_batch.restype = I
-        lib.exact_sdf_batch.argtypes = [P, P, P, I, P, I, P, P, P, P, P]
-        lib.mppi_step.restype = I
-        lib.mppi_step.argtypes = [P, P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
-        lib.mppi_step_predicted.restype = I
-        lib.mppi_step_predicted.argtypes = [P, P, P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
-        lib.exact_batch_create.restype = I
-        lib.exact_batch_create.argtypes = [I, P, ctypes.POINTER(P)]
-        lib.exact_batch_destroy.restype = V
-        lib.exact_batch_destroy.argtypes = [P]
-        lib.mppi_step_batched.restype = I
-        lib.mppi_step_batched.argtypes = [P, P]
-        lib.exact_batch_autotune.restype = I
-        lib.exact_batch_autotune.argtypes = [P, I, ctypes.c_char_p, I, P]
-        lib.exact_batch_get_tiles.restype = I
-        lib.exact_batch_get_tiles.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
-        lib.exact_batch_set_tiles.restype = I
-        lib.exact_batch_set_tiles.argtypes = [P, I, I]
-        lib.mppi_step_noalloc.restype = I
-        lib.mppi_step_noalloc.argtypes = [P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
-        F, LL = ctypes.c_float, ctypes.c_longlong
-        lib.exact_mlp_create.restype = I
-        lib.exact_mlp_create.argtypes = [I, I, I, I, ctypes.POINTER(P)]
-        lib.exact_mlp_destroy.restype = V
-        lib.exact_mlp_destroy.argtypes = [P]
-        lib.exact_mlp_num_params.restype = LL
-        lib.exact_mlp_num_params.argtypes = [P]
-        lib.exact_mlp_set_params.restype = I
-        lib.exact_mlp_set_params.argtypes = [P, P]
-        lib.exact_mlp_get_params.restype = I
-        lib.exact_mlp_get_params.argtypes = [P, P]
-        lib.exact_mlp_forward.restype = I
-        lib.exact_mlp_forward.argtypes = [P, P, I, P, P]
-        lib.exact_mlp_loss_grad.restype = I
-        lib.exact_mlp_loss_grad.argtypes = [P, P, P, I, P, P, P]
-        lib.exact_mlp_train_step.restype = I
-        lib.exact_mlp_train_step.argtypes = [P, P, P, I, F, P, P]
-        lib.exact_polar_hist.restype = I
-        lib.exact_polar_hist.argtypes = [P, P, I, I, P, I, F, P, P]
-        lib.exact_proposal_features.restype = I
-        lib.exact_proposal_features.argtypes = [P, I, F, P, P, P, P, I, I, P, P]
-        lib.exact_proposal_prepare.restype = I
-        lib.exact_proposal_prepare.argtypes = [P, P, LL, P, P, P]
-        lib.exact_proposal_select.restype = I
-        lib.exact_proposal_select.argtypes = [P, P, I, I, P, P, P, P, I, I, P, P, P, P]
-        lib.exact_hybrid_create.restype = I
-        lib.exact_hybrid_create.argtypes = [I, P, P, ctypes.POINTER(P)]
-        lib.exact_hybrid_destroy.restype = V
-        lib.exact_hybrid_destroy.argtypes = [P]
-        lib.mppi_step_hybrid.restype = I
-        lib.mppi_step_hybrid.argtypes = [P, P, P, P, P]
-        lib.exact_hybrid_batch.restype = P
-        lib.exact_hybrid_batch.argtypes = [P]
-        _lib = lib
-        return lib
+        _lib = _bind(ctypes.CDLL(_build.LIB_PATH))
+        return _lib
+
+
+_lib_debug = None
+
+
+def load_debug() -> ctypes.CDLL:
+    """Load the debug variant of the library (device-side index checks;
+    built by ``build.build(debug=True)``).  Its objects are its own: pass
+    them only to its functions."""
+    global _lib_debug
+    with _lock:
+        if _lib_debug is None:
+            if not os.path.exists(_build.LIB_PATH_DEBUG):
+                raise RuntimeError(f"{_build.LIB_PATH_DEBUG} is missing: build it with build.build(debug=True)")
+            _lib_debug = _bind(ctypes.CDLL(_build.LIB_PATH_DEBUG))
+        return _lib_debug
+
+
+def _bind(lib):
+    """Declare the argument and result types of every exported function."""
+    P, I, V = ctypes.c_void_p, ctypes.c_int, None
+    lib.exact_status_string.restype = ctypes.c_char_p
+    lib.exact_status_string.argtypes = [I]
+    lib.exact_footprint_create.restype = I
+    lib.exact_footprint_create.argtypes = [I, P, I, ctypes.POINTER(P)]
+    lib.exact_footprint_destroy.restype = V
+    lib.exact_footprint_destroy.argtypes = [P]
+    lib.exact_footprint_info.restype = I
+    lib.exact_footprint_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.exact_ctx_create.restype = I
+    lib.exact_ctx_create.argtypes = [ctypes.POINTER(P)]
+    lib.exact_ctx_destroy.restype = V
+    lib.exact_ctx_destroy.argtypes = [P]
+    lib.exact_ctx_reserve.restype = I
+    lib.exact_ctx_reserve.argtypes = [P, I, I, I]
+    lib.exact_ctx_reserve_cloud.restype = I
+    lib.exact_ctx_reserve_cloud.argtypes = [P, I, I, I, I]
+    lib.exact_ctx_get_error.restype = I
+    lib.exact_ctx_get_error.argtypes = [P, P]
+    lib.exact_batch_get_error.restype = I
+    lib.exact_batch_get_error.argtypes = [P, P]
+    lib.exact_sdf_batch.restype = I
+    lib.exact_sdf_batch.argtypes = [P, P, P, I, P, I, P, P, P, P, P]
+    lib.mppi_step.restype = I
+    lib.mppi_step.argtypes = [P, P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
+    lib.mppi_step_predicted.restype = I
+    lib.mppi_step_predicted.argtypes = [P, P, P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
+    lib.exact_batch_create.restype = I
+    lib.exact_batch_create.argtypes = [I, P, ctypes.POINTER(P)]
+    lib.exact_batch_destroy.restype = V
+    lib.exact_batch_destroy.argtypes = [P]
+    lib.mppi_step_batched.restype = I
+    lib.mppi_step_batched.argtypes = [P, P]
+    lib.exact_batch_autotune.restype = I
+    lib.exact_batch_autotune.argtypes = [P, I, ctypes.c_char_p, I, P]
+    lib.exact_batch_get_tiles.restype = I
+    lib.exact_batch_get_tiles.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.exact_batch_set_tiles.restype = I
+    lib.exact_batch_set_tiles.argtypes = [P, I, I]
+    lib.mppi_step_noalloc.restype = I
+    lib.mppi_step_noalloc.argtypes = [P, P, P, I, P, I, P, P, P, P, P, P, P, P, P, P, P]
+    F, LL = ctypes.c_float, ctypes.c_longlong
+    lib.exact_mlp_create.restype = I
+    lib.exact_mlp_create.argtypes = [I, I, I, I, ctypes.POINTER(P)]
+    lib.exact_mlp_destroy.restype = V
+    lib.exact_mlp_destroy.argtypes = [P]
+    lib.exact_mlp_num_params.restype = LL
+    lib.exact_mlp_num_params.argtypes = [P]
+    lib.exact_mlp_set_params.restype = I
+    lib.exact_mlp_set_params.argtypes = [P, P]
+    lib.exact_mlp_get_params.restype = I
+    lib.exact_mlp_get_params.argtypes = [P, P]
+    lib.exact_mlp_forward.restype = I
+    lib.exact_mlp_forward.argtypes = [P, P, I, P, P]
+    lib.exact_mlp_loss_grad.restype = I
+    lib.exact_mlp_loss_grad.argtypes = [P, P, P, I, P, P, P]
+    lib.exact_mlp_train_step.restype = I
+    lib.exact_mlp_train_step.argtypes = [P, P, P, I, F, P, P]
+    lib.exact_polar_hist.restype = I
+    lib.exact_polar_hist.argtypes = [P, P, I, I, P, I, F, P, P]
+    lib.exact_proposal_features.restype = I
+    lib.exact_proposal_features.argtypes = [P, I, F, P, P, P, P, I, I, P, P]
+    lib.exact_proposal_prepare.restype = I
+    lib.exact_proposal_prepare.argtypes = [P, P, LL, P, P, P]
+    lib.exact_proposal_select.restype = I
+    lib.exact_proposal_select.argtypes = [P, P, I, I, P, P, P, P, I, I, P, P, P, P]
+    lib.exact_hybrid_create.restype = I
+    lib.exact_hybrid_create.argtypes = [I, P, P, ctypes.POINTER(P)]
+    lib.exact_hybrid_destroy.restype = V
+    lib.exact_hybrid_destroy.argtypes = [P]
+    lib.mppi_step_hybrid.restype = I
+    lib.mppi_step_hybrid.argtypes = [P, P, P, P, P]
+    lib.exact_hybrid_batch.restype = P
+    lib.exact_hybrid_batch.argtypes = [P]
+    return lib
 
 
 def status_string(status: int) -> str:
@@ -229,8 +252,10 @@ class Context:
         _check(load().exact_ctx_reserve_cloud(self._h, max_poses, max_K, max_T, max_points),
                "exact_ctx_reserve_cloud")
 
-    def get_error(self) -> int:
-        return load().exact_ctx_get_error(self._h)
+    def get_error(self, stream=None) -> int:
+        """The context's device error word (0 = none), read and cleared in the
+        order of `stream` (default: the current stream), which is synchronised."""
+        return load().exact_ctx_get_error(self._h, _stream(stream))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -485,6 +510,11 @@ class Batch:
 
     def step(self, stream=None):
         _check(load().mppi_step_batched(self._h, _stream(stream)), "mppi_step_batched")
+
+    def get_error(self, stream=None) -> int:
+        """The batch's device error word (0 = none), read and cleared in the
+        order of `stream`, which is synchronised."""
+        return load().exact_batch_get_error(self._h, _stream(stream))
 
     def autotune(self, iters: int = 3, stream=None, cache: str | None = None) -> dict:
         """Pick the tile shape by timing the candidates (exact_batch_autotune).

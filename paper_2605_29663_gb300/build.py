@@ -2,7 +2,10 @@
 
 Compiles every translation unit under ``csrc/`` in parallel into
 ``_build/`` and links ``_lib/libexact_mppi.so``.  Rebuilds only when a
-source, a header or the flags changed.
+source, a header or the flags changed.  ``build(debug=True)`` makes the
+debug variant ``_lib/libexact_mppi_debug.so`` (``-DEXACT_DEBUG_CHECKS``:
+device-side index checks that record EXACT_ECAPACITY in the error word and
+skip the access) from ``_build_debug/``.
 """
 from __future__ import annotations
 
@@ -19,6 +22,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libexact_mppi.so")
+LIB_PATH_DEBUG = os.path.join(LIB_DIR, "libexact_mppi_debug.so")
+BUILD_DIR_DEBUG = os.path.join(PKG, "_build_debug")
 
 SOURCES = ["runtime.cu", "sdf_batch.cu", "mppi.cu", "batched.cu", "noalloc.cu", "mlp.cu", "features.cu", "hybrid.cu", "mppi_predicted.cu", "mppi_dense.cu", "batched_uniform_small.cu", "batched_uniform_large.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -45,21 +50,25 @@ def _fingerprint() -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if needed) and return the path of libexact_mppi.so."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: bool = False) -> str:
+    """Compile (if needed) and return the path of libexact_mppi.so (or of the
+    debug variant)."""
+    build_dir = BUILD_DIR_DEBUG if debug else BUILD_DIR
+    lib_path = LIB_PATH_DEBUG if debug else LIB_PATH
+    extra_flags = tuple(extra_flags) + (("-DEXACT_DEBUG_CHECKS",) if debug else ())
+    os.makedirs(build_dir, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
     fp = _fingerprint() + "|" + " ".join(extra_flags)
-    stamp = os.path.join(BUILD_DIR, "stamp")
-    if not force and os.path.exists(LIB_PATH) and os.path.exists(stamp):
+    stamp = os.path.join(build_dir, "stamp")
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read() == fp:
-                return LIB_PATH
+                return lib_path
     nvcc = _nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
         cmd = [nvcc, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -72,15 +81,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as f:
         f.write(fp)
-    return LIB_PATH
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -168,8 +168,9 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
     const size_t val_bytes = align_up(val.size() * sizeof(int2), 256);
     const size_t ctrl_bytes = align_up(kHdrStride * n_scenes + sizeof(unsigned), 256);
     const size_t sort_bytes = align_up(sort_list.size() * sizeof(int) + 1, 256);
+    const size_t err_bytes = 256;
     const size_t total =
-        2 * table_bytes + items_bytes + upd_bytes + val_bytes + ctrl_bytes + sort_bytes + scratch_total;
+        2 * table_bytes + items_bytes + upd_bytes + val_bytes + ctrl_bytes + sort_bytes + err_bytes + scratch_total;
 
     exact_batch *b = new (std::nothrow) exact_batch();
     if (!b) return EXACT_EINVAL;
@@ -183,6 +184,7 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
     b->d_ctrl = p; p += ctrl_bytes;
     b->d_sort = reinterpret_cast<int *>(p); p += sort_bytes;
     b->n_sort = (int)sort_list.size();
+    b->d_err = reinterpret_cast<int *>(p); p += err_bytes;
     char *scratch = p;
     b->ctrl_bytes = ctrl_bytes;
     b->d_queue = reinterpret_cast<unsigned *>(b->d_ctrl + kHdrStride * n_scenes);
@@ -213,6 +215,7 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         V.noise = S.noise;
         V.u_star = S.u_star; V.costs = S.costs; V.weights = S.weights; V.U_upd_out = S.U_upd;
         V.dmin = S.dmin; V.valid = S.valid; V.nom_cost = S.nom_cost;
+        V.err = b->d_err;
         V.hdr = reinterpret_cast<ArenaHeader *>(b->d_ctrl + kHdrStride * s);
         carve_scene(V, scratch + scratch_off[s], S.params.K, S.params.T, 1);
         D.src_pts = V.pts;
@@ -254,7 +257,7 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         cudaMemcpy(b->d_val, val.data(), val.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         (b->n_sort && cudaMemcpy(b->d_sort, sort_list.data(), sort_list.size() * sizeof(int), cudaMemcpyHostToDevice) !=
                           cudaSuccess) ||
-        cudaMemset(b->d_ctrl, 0, ctrl_bytes) != cudaSuccess ||
+        cudaMemset(b->d_ctrl, 0, ctrl_bytes) != cudaSuccess || cudaMemset(b->d_err, 0, err_bytes) != cudaSuccess ||
         (scratch_total && cudaMemset(scratch, 0, scratch_total) != cudaSuccess))
         rc = EXACT_ECUDA;
     if (rc == EXACT_OK) rc = batch_grid(b);
@@ -310,6 +313,16 @@ extern "C" int mppi_step_batched(exact_batch *b, void *stream) {
                                             (const SceneDev *)b->d_scenes, (const int2 *)b->d_val));
     return b->fp.kind == EXACT_FP_POLYGON && b->fp.n_pad > 16 ? launch_uniform_large(b, b->d_scenes, st, true)
                                                                : launch_uniform_small(b, b->d_scenes, st, true);
+}
+
+extern "C" int exact_batch_get_error(exact_batch *b, void *stream) {
+    if (!b) return EXACT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemsetAsync(b->d_err, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return EXACT_ECUDA;
+    return err;
 }
 
 extern "C" int exact_batch_get_tiles(const exact_batch *b, int *threads, int *pairs_per_lane) {

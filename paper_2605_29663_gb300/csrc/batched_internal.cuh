@@ -50,6 +50,7 @@ struct exact_batch {
     bool uniform = false;              // every scene has the same footprint constants
     exact_footprint fp;                // their copy (uniform batches)
     int grid_c = 0;                    // persistent grid of the constant-footprint kernel (0 = not yet known)
+    int *d_err = nullptr;              // device error word of the batch (not cleared by steps)
 };
 
 namespace exact {

@@ -18,6 +18,74 @@ constexpr unsigned long long kNoKey = ~0ull;
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
 
+// ---------------------------------------------------------------- device errors
+// A context (or batch) error word: the first nonzero exact_status a kernel
+// records stays until the host reads and clears it.  err may be NULL (no word).
+__device__ __forceinline__ void report_error(int *err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+// Index checks of the debug build (-DEXACT_DEBUG_CHECKS): a failed check
+// records EXACT_ECAPACITY and the caller skips the access.  In the release
+// build the condition is not evaluated.
+#ifdef EXACT_DEBUG_CHECKS
+#define EXACT_DCHECK(cond, err) ((cond) ? true : (::exact::report_error((err), EXACT_ECAPACITY), false))
+#else
+#define EXACT_DCHECK(cond, err) true
+#endif
+
+// ---------------------------------------------------------------- async copies
+// Bulk copies global -> shared memory on the TMA engine, completed on an
+// mbarrier (transaction bytes), and 8-byte cp.async copies (no register round
+// trip).  Waits on an mbarrier are bounded: kWaitTries polls (each suspends
+// the thread for a while), then the wait reports EXACT_ETIMEOUT and gives up.
+constexpr long long kWaitTries = 1ll << 22;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Arrive on the barrier announcing `bytes` of transactions for this phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of phase `parity`; false after kWaitTries polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    for (long long i = 0; i < kWaitTries; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// Orders this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// bytes (a multiple of 16) from 16-byte aligned global src to 16-byte aligned
+// shared dst, completing as transaction bytes on bar.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Two FP32 lanes in one 64-bit register pair, for the packed f32x2
 // arithmetic of sm_100-class GPUs: one instruction does the same IEEE
 // round-to-nearest operation on both lanes, so a packed chain gives the

@@ -105,6 +105,7 @@ int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const
     V.noise = noise;
     V.u_star = u_star; V.costs = costs; V.weights = weights; V.U_upd_out = U_upd; V.dmin = dmin; V.valid = valid;
     V.nom_cost = nullptr;
+    V.err = ctx->d_err;
     V.hdr = reinterpret_cast<ArenaHeader *>(ctx->scratch);
     carve_scene(V, static_cast<char *>(ctx->scratch) + kArenaHeader, P.K, P.T, parts);
     V.upd_chunk = upd_chunk_for(P.K, P.T, P.nu);

@@ -47,6 +47,7 @@ struct SceneView {
     float *u_star, *costs, *weights, *U_upd_out, *dmin;
     float *nom_cost;    // 1 or NULL: cost J of the updated nominal
     int *valid;
+    int *err;           // device error word (exact_status; first error kept), or NULL
     ArenaHeader *hdr;   // beta, tickets, validation flag
     double *Jt;         // K   J~ = J + w_inf I(chi)
     float *wt;          // K   unnormalised weights
@@ -538,7 +539,7 @@ template <bool MOVING = false, class EV>
 __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose,
                                                const float4 *cw, int h0, int nh, unsigned *keyh, int ppl,
                                                const float4 *circ, float cap, unsigned *msk, int *pre,
-                                               int *queue = nullptr) {
+                                               int *queue = nullptr, int *err = nullptr) {
     const int npairs = (n + 1) >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nsub = (n + kSub * ppl - 1) / (kSub * ppl);
@@ -642,7 +643,9 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
             const int a = 2 * lane;
             if (a < cnt) {
                 const bool two = a + 1 < cnt;
-                const int ea = q[a], eb = two ? q[a + 1] : ea;
+                int ea = q[a], eb = two ? q[a + 1] : ea;
+                if (!EXACT_DCHECK((ea & 4095) < n && (ea >> 12) < nh, err)) ea = 0;   // debug build: skip
+                if (!EXACT_DCHECK((eb & 4095) < n && (eb >> 12) < nh, err)) eb = 0;
                 const int ha = h0 + (ea >> 12), hb = h0 + (eb >> 12);
                 const float2 oa = point_at(ea & 4095, ha), ob = point_at(eb & 4095, hb);
                 const float4 pa = pose[ha], pb = pose[hb];
@@ -761,6 +764,7 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
                 if (e >= e1) return false;
                 while (m == 0ull) {
                     ++hh;
+                    if (!EXACT_DCHECK(hh < nh, err)) return false;
                     m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
                 }
                 cs = __ffsll((long long)m) - 1;
@@ -802,6 +806,7 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
     }
     float best = finf();
     for (int e = e0; e < e1; ++e) {
+        if (!EXACT_DCHECK(hh < nh, err)) break;
         while (m == 0ull) {   // step done: fold its minimum, move to the next step with entries
             best = warp_min_f(best);
             if (lane == 0 && best < finf()) atomicMin(keyh + h0 + hh, f2ord(best));
@@ -837,35 +842,78 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
     if (lane == 0 && best < finf()) atomicMin(keyh + h0 + hh, f2ord(best));
 }
 
-// Copy points [base, base + n) into shared memory, masked ones as NaN.
-// Eight loads per thread are in flight before the first store.  MOVING
-// stages (position, velocity) as one float4 per point.
+// Copy points [base, base + n) into shared memory, masked ones as NaN, with
+// the nt threads t0 = 0 .. nt - 1 of the calling group (a multiple of 32;
+// they meet on named barrier 1).  Static clouds whose source is 16-byte
+// aligned go through one TMA bulk copy (cp.async.bulk, completed on the
+// mbarrier bar, bounded wait; an odd last point by a plain load); predicted
+// clouds through 8-byte cp.async copies into the (position, velocity) float4
+// of each point.  Neither passes the points through registers.  After the
+// copies have landed, masked points are overwritten with NaN.  A source that
+// is only 8-byte aligned is staged through registers, eight loads per thread
+// in flight.  Ends without a block barrier: the caller synchronises.
 template <bool MOVING = false>
 __device__ __forceinline__ void stage_points(float2 *dst, const float2 *__restrict__ pts,
                                              const float2 *__restrict__ vel, const uint8_t *__restrict__ mask,
-                                             int base, int n, int t0, int nt) {
+                                             int base, int n, int t0, int nt, unsigned long long *bar, int *err) {
     const float qnan = __int_as_float(0x7fffffff);
-    for (int i0 = t0; i0 < n; i0 += 8 * nt) {
-        float2 p[8], v[8];
-        bool ok[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int i = i0 + k * nt;
-            p[k] = i < n ? __ldg(pts + base + i) : make_float2(0.f, 0.f);
-            if constexpr (MOVING) v[k] = i < n ? __ldg(vel + base + i) : make_float2(0.f, 0.f);
-            ok[k] = i < n && (!mask || __ldg(mask + base + i));
+    const bool aligned = ((uintptr_t)(pts + base) & 15u) == 0;
+    if (!MOVING && aligned) {
+        const int nb = n & ~1;   // points moved by the bulk copy (a multiple of 16 bytes)
+        if (t0 == 0 && nb > 0) {
+            mbar_init(bar, 1);
+            fence_proxy_async_smem();   // earlier reads of the stage come before the copy's writes
+            mbar_arrive_expect_tx(bar, (unsigned)nb * sizeof(float2));
+            bulk_copy_g2s(dst, pts + base, (unsigned)nb * sizeof(float2), bar);
         }
+        if (t0 == 0 && nb < n) dst[nb] = __ldg(pts + base + nb);
+        asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");   // the barrier is initialised
+        if (nb > 0 && !mbar_wait(bar, 0)) {
+            report_error(err, EXACT_ETIMEOUT);
+            mbar_wait(bar, 0);   // once more for the copy still in flight, then go on
+        }
+    } else if (MOVING) {   // positions and velocities are 8-byte aligned (checked by the host)
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (int i = t0; i < n; i += nt) {
+            cp_async8(&d4[i].x, pts + base + i);
+            cp_async8(&d4[i].z, vel + base + i);
+        }
+        cp_async_wait_all();
+    } else {
+        for (int i0 = t0; i0 < n; i0 += 8 * nt) {   // static cloud, source only 8-byte aligned
+            float2 p[8], v[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int i = i0 + k * nt;
-            if (i < n) {
-                const float2 q = ok[k] ? p[k] : make_float2(qnan, qnan);
-                if constexpr (MOVING)
-                    reinterpret_cast<float4 *>(dst)[i] = make_float4(q.x, q.y, v[k].x, v[k].y);
-                else
-                    dst[i] = q;
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * nt;
+                p[k] = i < n ? __ldg(pts + base + i) : make_float2(0.f, 0.f);
+                if constexpr (MOVING) v[k] = i < n ? __ldg(vel + base + i) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * nt;
+                if (i < n) {
+                    if constexpr (MOVING)
+                        reinterpret_cast<float4 *>(dst)[i] = make_float4(p[k].x, p[k].y, v[k].x, v[k].y);
+                    else
+                        dst[i] = p[k];
+                }
             }
         }
+    }
+    if (mask) {
+        // after the copies: masked points become NaN (every evaluator turns
+        // them into a +inf key); a point's copy and its overwrite are made by
+        // the same thread, or ordered by the completed wait (bulk copy) and
+        // the named barrier (odd last point)
+        for (int i = t0; i < n; i += nt)
+            if (!__ldg(mask + base + i)) {
+                if constexpr (MOVING) {
+                    reinterpret_cast<float4 *>(dst)[i].x = qnan;
+                    reinterpret_cast<float4 *>(dst)[i].y = qnan;
+                } else {
+                    dst[i] = make_float2(qnan, qnan);
+                }
+            }
     }
 }
 
@@ -889,6 +937,7 @@ struct SampleSmem {
     float4 pose[EXACT_MAX_HORIZON];
     float stage[EXACT_MAX_HORIZON];
     unsigned key[EXACT_MAX_HORIZON];
+    unsigned long long bar;            // mbarrier of the bulk copy that stages the points
     float term[2];
     bool last;
 };
@@ -922,6 +971,9 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     const int h0 = (p * T) / V.parts, h1 = ((p + 1) * T) / V.parts;
     const int k0 = ns == 2 ? 0 : h0, nk = ns == 2 ? 2 * T : h1 - h0;   // step slots [k0, k0 + nk)
     for (int h = k0 + (int)threadIdx.x; h < k0 + nk; h += blockDim.x) sm.key[h] = f2ord(finf());
+    if (r == 0 && p == 0 && threadIdx.x == 0 &&
+        !(isfinite(V.state[0]) && isfinite(V.state[1]) && isfinite(V.state[2])))
+        report_error(V.err, EXACT_EINVAL);   // a start state the host could not see is not finite
     const int n0 = min(N, kS);
     const float3 bc = ev.bound();
     const int warp = threadIdx.x >> 5;
@@ -952,7 +1004,8 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     } else {
         grid_dep_wait();
         if (!staged)
-            stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, 0, n0, threadIdx.x - 32 * ns, blockDim.x - 32 * ns);
+            stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, 0, n0, threadIdx.x - 32 * ns, blockDim.x - 32 * ns, &sm.bar,
+                                 V.err);
     }
     __syncthreads();
     const bool prune = !V.dmin && N >= kPruneMin;
@@ -971,11 +1024,11 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     // clouds, one pass) are skipped
     const float cap = V.dmin ? -1.f : fmaxf(P.d_safe, 0.f);
     steps_min_keys<MOVING>(ev, s_pts, n0, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
-                           sm.pre, !V.dmin && N < kPruneMin ? sm.queue : nullptr);
+                           sm.pre, !V.dmin && N < kPruneMin ? sm.queue : nullptr, V.err);
     for (int base = kS; base < N; base += kS) {   // clouds larger than the stage
         const int n = min(kS, N - base);
         __syncthreads();
-        stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, base, n, threadIdx.x, blockDim.x);
+        stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, base, n, threadIdx.x, blockDim.x, &sm.bar, V.err);
         __syncthreads();
         if (prune) {
             if (pre_circ)
@@ -985,7 +1038,7 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
             __syncthreads();
         }
         steps_min_keys<MOVING>(ev, s_pts, n, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
-                               sm.pre);
+                               sm.pre, nullptr, V.err);
     }
     grid_dep_release();
     __syncthreads();
@@ -1047,6 +1100,7 @@ __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSme
 
     const float *src = V.noise + (size_t)r0 * TN;
     const int n = nr * TN;
+    bool finite = true;
     for (int i0 = tid; i0 < n; i0 += 8 * kUpdBlock) {
         float v[8];
 #pragma unroll
@@ -1059,10 +1113,14 @@ __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSme
             const int i = i0 + k * kUpdBlock;
             if (i < n) {
                 const int e = i % TN;
+                finite &= isfinite(v[k]);
                 sm.tile[i] = P.clamp ? clamp_u(P, e % nu, U[e] + v[k]) - U[e] : v[k];
             }
         }
     }
+    if (b == 0)
+        for (int e = tid; e < TN; e += kUpdBlock) finite &= isfinite(U[e]);
+    if (!finite) report_error(V.err, EXACT_EINVAL);   // non-finite noise or nominal (device data)
     grid_dep_wait();   // J~ and beta come from the sample phase
     const double beta = ord2d(~V.hdr->beta_enc);
     if (V.parts > 1)   // the sample phase is over: rearm its per-sample part tickets
@@ -1127,6 +1185,7 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
     const int K = P.K, T = P.T, nu = P.nu, TN = T * nu, G = V.upd_blocks;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nblocks = T * V.val_chunks, self = h * V.val_chunks + c;
+    if (!EXACT_DCHECK(h < T && c < V.val_chunks, V.err)) return;   // debug build: a block outside the table
     // the nominal U and the start state stay unchanged until this kernel's
     // last block: read them while the update phase drains
     for (int e = tid; e < TN; e += kBlock) sm.U[e] = V.U[e];

@@ -81,6 +81,7 @@ extern "C" int mppi_step_noalloc(const float *state, const float *cloud, const u
     V.noise = noise;
     V.u_star = u_star; V.costs = costs; V.weights = weights; V.U_upd_out = U_upd; V.dmin = dmin; V.valid = valid;
     V.nom_cost = nullptr;
+    V.err = nullptr;   // no context: device-side errors are not recorded
     V.vel = nullptr;
     V.hdr = reinterpret_cast<ArenaHeader *>(arena);
     carve_scene(V, static_cast<char *>(arena) + kArenaHeader, P.K, P.T, parts);

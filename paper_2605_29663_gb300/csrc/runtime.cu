@@ -242,11 +242,13 @@ extern "C" void exact_ctx_destroy(exact_ctx *ctx) {
     delete ctx;
 }
 
-extern "C" int exact_ctx_get_error(exact_ctx *ctx) {
+extern "C" int exact_ctx_get_error(exact_ctx *ctx, void *stream) {
     if (!ctx) return EXACT_EINVAL;
-    if (cudaDeviceSynchronize() != cudaSuccess) return EXACT_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
     int err = 0;
-    if (cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return EXACT_ECUDA;
-    if (cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) return EXACT_ECUDA;
+    // read and clear in stream order, then wait for this stream only
+    if (cudaMemcpyAsync(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return EXACT_ECUDA;
     return err;
 }

@@ -130,10 +130,12 @@ __global__ void __launch_bounds__(kSdfBlock)
 sdf_batch_kernel(const float2 *__restrict__ pts, const uint8_t *__restrict__ mask, int N,
                  const float *__restrict__ poses, const FPC fpc, float *__restrict__ dist, int vec_store,
                  float *__restrict__ dmin, int *__restrict__ argmin,
-                 unsigned long long *__restrict__ keys, int chunks, int chunk_pairs) {
+                 unsigned long long *__restrict__ keys, int chunks, int chunk_pairs, int *err) {
     const int pose = blockIdx.x / chunks;
     const int chunk = blockIdx.x - pose * chunks;
     const float tx = poses[3 * (size_t)pose], ty = poses[3 * (size_t)pose + 1], th = poses[3 * (size_t)pose + 2];
+    if (chunk == 0 && threadIdx.x == 0 && !(isfinite(tx) && isfinite(ty) && isfinite(th)))
+        report_error(err, EXACT_EINVAL);   // non-finite pose (device data)
     float sn, cs;
     sincosf(th, &sn, &cs);
     const int npairs = (N + 1) >> 1;
@@ -263,7 +265,7 @@ extern "C" int exact_sdf_batch(exact_ctx *ctx, const float *points, const uint8_
         auto k = mask ? (dist ? sdf_batch_kernel<FPC, true, true> : sdf_batch_kernel<FPC, false, true>)
                       : (dist ? sdf_batch_kernel<FPC, true, false> : sdf_batch_kernel<FPC, false, false>);
         k<<<grid, kSdfBlock, 0, st>>>(p2, mask, n_points, poses, fpc, dist, vec, dmin, argmin, keys, chunks,
-                                   chunk_pairs);
+                                   chunk_pairs, ctx ? ctx->d_err : nullptr);
         if (keys)
             sdf_keys_finish<FPC><<<(n_poses + 255) / 256, 256, 0, st>>>(keys, n_poses, fpc, dmin, argmin);
         return cuda_status(cudaGetLastError());
