@@ -483,104 +483,99 @@ def oracle_mppi_sample(s, budget_s: float = 3.0) -> dict:
             "kind": "oracle", "sample": f"{n} full cycles of the same scene, float64, OpenMP over samples"}
 
 
-def batched_extra(torch, ex, dev, steps=3, tune=True):
-    """The 64-scene heterogeneous batch: one persistent launch per step vs the
-    same scenes as 64 consecutive single-scene mppi_step calls."""
-    import synth
-    scenes = synth.batched(0)
-    devs = []
-    for s in scenes:
-        devs.append(dict(state=torch.from_numpy(s["q0"]).to(dev), cloud=torch.from_numpy(s["cloud"]).to(dev),
-                         waypoints=torch.from_numpy(s["waypoints"]).to(dev), U=torch.from_numpy(s["U"]).to(dev),
-                         noise=torch.from_numpy(s["eps"]).to(dev),
-                         mask=None if s["mask"] is None else torch.from_numpy(s["mask"]).to(dev),
-                         fp=ex.Footprint(s["kind"], s["fp"]), params=s["params"]))
-    evals = sum(s["params"]["K"] * s["params"]["T"] * s["cloud"].shape[0] * s["fp"].shape[0] for s in scenes)
+def _batch_vs_singles(torch, ex, dev, scenes, steps):
+    """Time the batched step of `scenes` (persistent launch set, captured in a
+    CUDA graph and replayed; also eager) against the same scenes as
+    consecutive single-scene mppi_step calls (eager, and captured in one
+    graph).  Every arm starts from the same nominal sequences."""
+    devs = [dict(state=torch.from_numpy(s["q0"]).to(dev), cloud=torch.from_numpy(s["cloud"]).to(dev),
+                 waypoints=torch.from_numpy(s["waypoints"]).to(dev), U=torch.from_numpy(s["U"]).to(dev),
+                 noise=torch.from_numpy(s["eps"]).to(dev),
+                 mask=None if s["mask"] is None else torch.from_numpy(s["mask"]).to(dev),
+                 fp=ex.Footprint(s["kind"], s["fp"]), params=s["params"]) for s in scenes]
+    U0 = [d["U"].clone() for d in devs]
+
+    def reset():
+        for d, u in zip(devs, U0):
+            d["U"].copy_(u)
+
+    def timed(fn):
+        reset()
+        fn()
+        reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
     b = ex.Batch(devs)
-    report = b.autotune(iters=1) if tune else None
-    b.step()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        b.step()
-    e1.record()
-    torch.cuda.synchronize()
-    ms_b = e0.elapsed_time(e1) / steps
+    report = b.autotune(iters=1)
+    side = torch.cuda.Stream(device=dev)
+    gb = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(gb, stream=side):
+            b.step()
+    ms_graph = timed(gb.replay)
+    ms_eager = timed(b.step)
     ctx = ex.Context()
     ctx.reserve(0, max(s["params"]["K"] for s in scenes), max(s["params"]["T"] for s in scenes),
                 max(s["cloud"].shape[0] for s in scenes))
     outs = [dict() for _ in devs]
 
-    def singles():
+    def singles(stream=None):
         for d, o in zip(devs, outs):
             o.update(ex.mppi_step(ctx, d["state"], d["cloud"], d["waypoints"], d["U"], d["noise"], d["fp"],
-                                  d["params"], mask=d["mask"], out=o))
+                                  d["params"], mask=d["mask"], out=o, stream=stream))
 
     singles()
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(steps):
-        singles()
-    e1.record()
-    torch.cuda.synchronize()
-    ms_s = e0.elapsed_time(e1) / steps
-    return {"scenes": len(scenes), "point_edge_evals_per_step": evals,
-            "batched_ms_per_step": ms_b, "batched_scene_steps_per_s": len(scenes) * 1e3 / ms_b,
-            "batched_counted_tflops": FLOPS_PER_POINT_EDGE * evals / (ms_b * 1e-3) / 1e12,
-            "single_launches_ms_per_step": ms_s, "single_scene_steps_per_s": len(scenes) * 1e3 / ms_s,
-            "speedup_vs_single_launches": ms_s / ms_b, "tiles": list(b.tiles),
-            "autotune": report, "launches_per_step": 3,
-            "timing": "events over consecutive steps (no graph); same scenes, same GPU"}
+    gs = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        torch.cuda.synchronize()
+        with torch.cuda.graph(gs, stream=side):
+            singles(side)
+    ms_s = timed(singles)
+    ms_sg = timed(gs.replay)
+    n = len(scenes)
+    return {"scenes": n, "batched_ms_per_step": ms_graph, "batched_eager_ms_per_step": ms_eager,
+            "batched_scene_steps_per_s": n * 1e3 / ms_graph,
+            "single_launches_ms_per_step": ms_s, "single_launches_graph_ms_per_step": ms_sg,
+            "single_scene_steps_per_s": n * 1e3 / ms_s,
+            "speedup_vs_single_launches": ms_s / ms_graph, "speedup_vs_single_launches_graph": ms_sg / ms_graph,
+            "tiles": list(b.tiles), "autotune": report,
+            "timing": f"{steps} consecutive cycles per arm from the same nominals, CUDA events; batched = one "
+                      "captured step replayed; singles = consecutive mppi_step calls (eager, and the same "
+                      "calls captured in one graph)"}
+
+
+def batched_extra(torch, ex, dev, steps=3):
+    """The 64-scene heterogeneous batch (persistent launch set in a CUDA
+    graph) against the same scenes as 64 consecutive single-scene calls."""
+    import synth
+    scenes = synth.batched(0)
+    out = _batch_vs_singles(torch, ex, dev, scenes, steps)
+    evals = sum(s["params"]["K"] * s["params"]["T"] * s["cloud"].shape[0] * s["fp"].shape[0] for s in scenes)
+    out.update({"point_edge_evals_per_step": evals,
+                "batched_counted_tflops": FLOPS_PER_POINT_EDGE * evals / (out["batched_ms_per_step"] * 1e-3) / 1e12,
+                "launches_per_step": 3})
+    return out
 
 
 def batched_small_extra(torch, ex, dev, n_scenes=128, steps=5):
     """Many small scenes (K = 256, T = 20, N = 512, star polygons of 4-16
-    vertices, diff / Ackermann / omni): one batched step against the same
+    vertices, diff / Ackermann / omni): the batched step against the same
     scenes as consecutive single-scene mppi_step calls; here the per-call
     launches dominate and the persistent launch pays."""
     import synth
     g = synth.rng(5)
     scenes = [synth.random_scene(g, [synth.DIFF, synth.ACKERMANN, synth.OMNI][i % 3], int(g.integers(4, 17)), 512,
                                  256, 20) for i in range(n_scenes)]
-    devs = [dict(state=torch.from_numpy(s["q0"]).to(dev), cloud=torch.from_numpy(s["cloud"]).to(dev),
-                 waypoints=torch.from_numpy(s["waypoints"]).to(dev), U=torch.from_numpy(s["U"]).to(dev),
-                 noise=torch.from_numpy(s["eps"]).to(dev),
-                 mask=None if s["mask"] is None else torch.from_numpy(s["mask"]).to(dev),
-                 fp=ex.Footprint(s["kind"], s["fp"]), params=s["params"]) for s in scenes]
-    b = ex.Batch(devs)
-    b.autotune(iters=1)
-    b.step()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        b.step()
-    e1.record()
-    torch.cuda.synchronize()
-    ms_b = e0.elapsed_time(e1) / steps
-    ctx = ex.Context()
-    ctx.reserve(0, 256, 20, 512)
-    outs = [dict() for _ in devs]
-
-    def singles():
-        for d, o in zip(devs, outs):
-            o.update(ex.mppi_step(ctx, d["state"], d["cloud"], d["waypoints"], d["U"], d["noise"], d["fp"],
-                                  d["params"], mask=d["mask"], out=o))
-
-    singles()
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(steps):
-        singles()
-    e1.record()
-    torch.cuda.synchronize()
-    ms_s = e0.elapsed_time(e1) / steps
-    return {"scenes": n_scenes, "K": 256, "T": 20, "N": 512, "edges": "4-16",
-            "batched_ms_per_step": ms_b, "batched_scene_steps_per_s": n_scenes * 1e3 / ms_b,
-            "single_launches_ms_per_step": ms_s, "single_scene_steps_per_s": n_scenes * 1e3 / ms_s,
-            "speedup_vs_single_launches": ms_s / ms_b, "tiles": list(b.tiles),
-            "timing": "events over consecutive steps (no graph); same scenes, same GPU"}
+    out = _batch_vs_singles(torch, ex, dev, scenes, steps)
+    out.update({"K": 256, "T": 20, "N": 512, "edges": "4-16"})
+    return out
 
 
 def run_mppi_workload(args):
@@ -673,7 +668,8 @@ def mppi_summary(extra: dict) -> dict:
             out[key] = {"batched_ms_per_step": round(b["batched_ms_per_step"], 3),
                         "single_launches_ms_per_step": round(b["single_launches_ms_per_step"], 3),
                         "speedup_vs_single_launches": round(b["speedup_vs_single_launches"], 3),
-                        "timing": b.get("timing", "")}
+                        "speedup_vs_single_launches_graph": round(b["speedup_vs_single_launches_graph"], 3),
+                        "timing": "batched step replayed from a CUDA graph; singles eager / in a graph"}
     return out
 
 

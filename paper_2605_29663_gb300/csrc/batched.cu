@@ -44,6 +44,7 @@ batched_sample_kernel(const SceneDev *__restrict__ scenes, const int2 *__restric
     float2 *s_pts = reinterpret_cast<float2 *>(dyn + kFpSlots);
     __shared__ SampleSmem sm;
     __shared__ int s_item;
+    sample_smem_init(sm);
     int fp_scene = -1, pts_scene = -1;   // block-uniform
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);

@@ -19,6 +19,7 @@ batched_sample_kernel_c(const SceneDev *__restrict__ scenes, const int2 *__restr
     float2 *s_pts = reinterpret_cast<float2 *>(dyn + kFpSlots);
     __shared__ SampleSmem sm;
     __shared__ int s_item;
+    sample_smem_init(sm);
     int pts_scene = -1;   // block-uniform
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);

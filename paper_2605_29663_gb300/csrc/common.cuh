@@ -36,9 +36,16 @@ __device__ __forceinline__ void report_error(int *err, int code) {
 // ---------------------------------------------------------------- async copies
 // Bulk copies global -> shared memory on the TMA engine, completed on an
 // mbarrier (transaction bytes), and 8-byte cp.async copies (no register round
-// trip).  Waits on an mbarrier are bounded: kWaitTries polls (each suspends
-// the thread for a while), then the wait reports EXACT_ETIMEOUT and gives up.
-constexpr long long kWaitTries = 1ll << 22;
+// trip).  An mbarrier is initialised once per kernel and its phases are
+// counted; a wait on a phase is bounded by kWaitNs of wall time, after which
+// it reports EXACT_ETIMEOUT and gives up.
+constexpr unsigned long long kWaitNs = 20ull * 1000 * 1000;   // 20 ms
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -60,11 +67,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the completion of phase `parity`; false after kWaitTries polls.
+// Bounded wait for the completion of phase `parity`; false after kWaitNs.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-    for (long long i = 0; i < kWaitTries; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitNs) return false;
+    return true;
 }
 // Orders this thread's earlier generic-proxy accesses of shared memory before
 // later async-proxy (bulk copy) accesses.

@@ -846,7 +846,8 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
 // the nt threads t0 = 0 .. nt - 1 of the calling group (a multiple of 32;
 // they meet on named barrier 1).  Static clouds whose source is 16-byte
 // aligned go through one TMA bulk copy (cp.async.bulk, completed on the
-// mbarrier bar, bounded wait; an odd last point by a plain load); predicted
+// mbarrier bar, initialised once per kernel, whose completed phases *uses
+// counts; bounded wait; an odd last point by a plain load); predicted
 // clouds through 8-byte cp.async copies into the (position, velocity) float4
 // of each point.  Neither passes the points through registers.  After the
 // copies have landed, masked points are overwritten with NaN.  A source that
@@ -855,22 +856,26 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
 template <bool MOVING = false>
 __device__ __forceinline__ void stage_points(float2 *dst, const float2 *__restrict__ pts,
                                              const float2 *__restrict__ vel, const uint8_t *__restrict__ mask,
-                                             int base, int n, int t0, int nt, unsigned long long *bar, int *err) {
+                                             int base, int n, int t0, int nt, unsigned long long *bar,
+                                             unsigned *uses, int *err) {
     const float qnan = __int_as_float(0x7fffffff);
     const bool aligned = ((uintptr_t)(pts + base) & 15u) == 0;
     if (!MOVING && aligned) {
         const int nb = n & ~1;   // points moved by the bulk copy (a multiple of 16 bytes)
+        const unsigned parity = *uses & 1u;   // the phase this copy completes
         if (t0 == 0 && nb > 0) {
-            mbar_init(bar, 1);
             fence_proxy_async_smem();   // earlier reads of the stage come before the copy's writes
             mbar_arrive_expect_tx(bar, (unsigned)nb * sizeof(float2));
             bulk_copy_g2s(dst, pts + base, (unsigned)nb * sizeof(float2), bar);
         }
         if (t0 == 0 && nb < n) dst[nb] = __ldg(pts + base + nb);
-        asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");   // the barrier is initialised
-        if (nb > 0 && !mbar_wait(bar, 0)) {
-            report_error(err, EXACT_ETIMEOUT);
-            mbar_wait(bar, 0);   // once more for the copy still in flight, then go on
+        asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");   // every thread has read *uses
+        if (nb > 0) {
+            if (!mbar_wait(bar, parity)) {
+                report_error(err, EXACT_ETIMEOUT);
+                mbar_wait(bar, parity);   // once more for the copy still in flight, then go on
+            }
+            if (t0 == 0) *uses += 1u;   // read again only after the caller's block barrier
         }
     } else if (MOVING) {   // positions and velocities are 8-byte aligned (checked by the host)
         float4 *d4 = reinterpret_cast<float4 *>(dst);
@@ -937,10 +942,21 @@ struct SampleSmem {
     float4 pose[EXACT_MAX_HORIZON];
     float stage[EXACT_MAX_HORIZON];
     unsigned key[EXACT_MAX_HORIZON];
-    unsigned long long bar;            // mbarrier of the bulk copy that stages the points
+    unsigned long long bar;            // mbarrier of the bulk copies that stage the points
+    unsigned bar_uses;                 // its completed phases
     float term[2];
     bool last;
 };
+
+// Every kernel that runs sample_body starts with this (thread 0 initialises
+// the staging mbarrier; all threads then pass a block barrier).
+__device__ __forceinline__ void sample_smem_init(SampleSmem &sm) {
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar, 1);
+        sm.bar_uses = 0u;
+    }
+    __syncthreads();
+}
 
 // Horizon part p of sample r of a scene (steps [p T / parts, (p+1) T / parts)).
 // s_pts holds min(N, kStage) points; when `staged` is true the first chunk
@@ -1005,7 +1021,7 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
         grid_dep_wait();
         if (!staged)
             stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, 0, n0, threadIdx.x - 32 * ns, blockDim.x - 32 * ns, &sm.bar,
-                                 V.err);
+                                 &sm.bar_uses, V.err);
     }
     __syncthreads();
     const bool prune = !V.dmin && N >= kPruneMin;
@@ -1028,7 +1044,8 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     for (int base = kS; base < N; base += kS) {   // clouds larger than the stage
         const int n = min(kS, N - base);
         __syncthreads();
-        stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, base, n, threadIdx.x, blockDim.x, &sm.bar, V.err);
+        stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, base, n, threadIdx.x, blockDim.x, &sm.bar, &sm.bar_uses,
+                             V.err);
         __syncthreads();
         if (prune) {
             if (pre_circ)

@@ -19,6 +19,7 @@ __global__ void __launch_bounds__(kBlock, MINB)
 mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev, const float4 *circ, int pair) {
     extern __shared__ float2 s_pts[];   // min(N, stage) staged points (float4 each when MOVING)
     __shared__ SampleSmem sm;
+    sample_smem_init(sm);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // the validation kernel that follows on the stream counts its
         // finished blocks on this ticket: start it from zero

@@ -233,3 +233,36 @@ def test_paired_items_equal_single_scene_bitwise(ex, shared_fp, dmin):
             if key in ref:
                 np.testing.assert_array_equal(got[i][key], ref[key], err_msg=f"scene {i} {key}")
         assert got[i]["valid"] == ref["valid"]
+
+
+@pytest.mark.parametrize("shared_fp", [False, True])
+def test_batched_step_captured_in_a_cuda_graph(ex, shared_fp):
+    """The whole batched control step (memset, ordering, persistent sample
+    kernel, update, validation) captured once in a CUDA graph and replayed
+    for three consecutive cycles gives, after every cycle, the bits of three
+    eager steps of an identical batch: outputs and the shifted nominals."""
+    import torch
+    scenes = synth.batched(31, n_scenes=10, scale=0.3)
+    if shared_fp:
+        for s in scenes:
+            s["kind"], s["fp"] = synth.POLYGON, synth.l_footprint()
+    eager = [_dev_scene(ex, s) for s in scenes]
+    graph = [_dev_scene(ex, s) for s in scenes]
+    be, bg = ex.Batch(eager), ex.Batch(graph)
+    st = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            bg.step()
+    torch.cuda.synchronize()
+    for cycle in range(3):
+        be.step()
+        g.replay()
+        torch.cuda.synchronize()
+        for i, (de, dg, oe, og) in enumerate(zip(eager, graph, be.outputs, bg.outputs)):
+            for k in oe:
+                np.testing.assert_array_equal(og[k].cpu().numpy(), oe[k].cpu().numpy(),
+                                              err_msg=f"cycle {cycle} scene {i} {k}")
+            np.testing.assert_array_equal(dg["U"].cpu().numpy(), de["U"].cpu().numpy(),
+                                          err_msg=f"cycle {cycle} scene {i} U")
+    assert be.get_error() == 0 and bg.get_error() == 0
