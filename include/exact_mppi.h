@@ -112,6 +112,26 @@ int exact_ctx_reserve_cloud(exact_ctx *ctx, int max_poses, int max_K, int max_T,
  * and the rest of the device are not waited for. */
 int exact_ctx_get_error(exact_ctx *ctx, void *stream);
 
+/* Cycle statistics of the MPPI steps run with a context (Sec. III-E weights;
+ * diagnostics, the paper reports none): after exact_ctx_enable_stats(ctx, 1)
+ * every mppi_step / mppi_step_predicted on ctx also launches one small
+ * kernel that records, for that cycle, the effective sample size
+ * ESS = 1 / sum_r omega_r^2 of the normalised weights, the minimum and mean
+ * of J~, whether the updated nominal passed validation, and counts the
+ * cycles and the validation failures since the counters were last read.
+ * exact_ctx_get_stats reads (and zeroes the counters) in the order of
+ * `stream`, which is then synchronised.  Statistics are off by default
+ * (enabling allocates nothing; the record lives in the context). */
+typedef struct {
+    long long cycles;                /* cycles recorded since the last read */
+    long long validation_failures;   /* of which failed validation */
+    float ess;                       /* last cycle: 1 / sum omega^2, in [1, K] */
+    float cost_min, cost_mean;       /* last cycle: min and mean of J~ */
+    int last_valid;                  /* last cycle: 1 if the updated nominal passed */
+} exact_cycle_stats;
+int exact_ctx_enable_stats(exact_ctx *ctx, int enable);
+int exact_ctx_get_stats(exact_ctx *ctx, exact_cycle_stats *out, void *stream);
+
 /* ------------------------------------------------------------------ SDF batch
  * Batched exact signed distance (Sec. IV-C, IV-D; the evaluator of
  * Experiment 1).  For pose p = (x, y, theta) and point o_i every point is
@@ -213,6 +233,14 @@ long long exact_mlp_num_params(const exact_mlp *m);
 /* host packed parameters in / out (synchronous); set resets Adam */
 int exact_mlp_set_params(exact_mlp *m, const float *host_params);
 int exact_mlp_get_params(const exact_mlp *m, float *host_params);
+/* The whole training state for a checkpoint (synchronous): parameters and
+ * Adam's first and second moments (host, exact_mlp_num_params floats each)
+ * and the Adam step count.  Setting a state got from another object of the
+ * same shape resumes training exactly: the next steps give the same bits as
+ * the uninterrupted run (every kernel reduces in a fixed order). */
+int exact_mlp_get_state(const exact_mlp *m, float *host_params, float *host_m, float *host_v, long long *step);
+int exact_mlp_set_state(exact_mlp *m, const float *host_params, const float *host_m, const float *host_v,
+                        long long step);
 /* x device B x d_in -> y device B x d_out */
 int exact_mlp_forward(exact_mlp *m, const float *x, int B, float *y, void *stream);
 /* loss (device 1 float, or NULL) and gradients (device packed vector, or

@@ -30,7 +30,8 @@ EXPORTS = ["exact_status_string", "exact_footprint_create", "exact_footprint_des
            "exact_ctx_get_error", "exact_sdf_batch", "mppi_step", "mppi_step_predicted", "exact_batch_create",
            "exact_batch_destroy",
            "mppi_step_batched", "exact_batch_autotune", "exact_batch_get_tiles", "exact_batch_set_tiles",
-           "exact_batch_get_error",
+           "exact_batch_get_error", "exact_ctx_enable_stats", "exact_ctx_get_stats", "exact_mlp_get_state",
+           "exact_mlp_set_state",
            "mppi_step_noalloc", "exact_mlp_create", "exact_mlp_destroy", "exact_mlp_num_params",
            "exact_mlp_set_params", "exact_mlp_get_params", "exact_mlp_forward", "exact_mlp_loss_grad",
            "exact_mlp_train_step", "exact_polar_hist", "exact_proposal_features", "exact_proposal_prepare",
@@ -45,6 +46,12 @@ class ExactError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {status_string(status)} (status {status})")
         self.status = status
+
+
+class CycleStats(ctypes.Structure):
+    """Mirror of exact_cycle_stats."""
+    _fields_ = [("cycles", ctypes.c_longlong), ("validation_failures", ctypes.c_longlong), ("ess", ctypes.c_float),
+                ("cost_min", ctypes.c_float), ("cost_mean", ctypes.c_float), ("last_valid", ctypes.c_int)]
 
 
 def load() -> ctypes.CDLL:
@@ -99,6 +106,14 @@ def _bind(lib):
     lib.exact_ctx_get_error.argtypes = [P, P]
     lib.exact_batch_get_error.restype = I
     lib.exact_batch_get_error.argtypes = [P, P]
+    lib.exact_ctx_enable_stats.restype = I
+    lib.exact_ctx_enable_stats.argtypes = [P, I]
+    lib.exact_ctx_get_stats.restype = I
+    lib.exact_ctx_get_stats.argtypes = [P, ctypes.POINTER(CycleStats), P]
+    lib.exact_mlp_get_state.restype = I
+    lib.exact_mlp_get_state.argtypes = [P, P, P, P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.exact_mlp_set_state.restype = I
+    lib.exact_mlp_set_state.argtypes = [P, P, P, P, ctypes.c_longlong]
     lib.exact_sdf_batch.restype = I
     lib.exact_sdf_batch.argtypes = [P, P, P, I, P, I, P, P, P, P, P]
     lib.mppi_step.restype = I
@@ -256,6 +271,17 @@ class Context:
         """The context's device error word (0 = none), read and cleared in the
         order of `stream` (default: the current stream), which is synchronised."""
         return load().exact_ctx_get_error(self._h, _stream(stream))
+
+    def enable_stats(self, enable: bool = True):
+        """Record per-cycle statistics (ESS, J~ min / mean, validation) of the
+        MPPI steps run with this context."""
+        _check(load().exact_ctx_enable_stats(self._h, int(bool(enable))), "exact_ctx_enable_stats")
+
+    def get_stats(self, stream=None) -> dict:
+        """The statistics record (its counters are zeroed by the read)."""
+        st = CycleStats()
+        _check(load().exact_ctx_get_stats(self._h, ctypes.byref(st), _stream(stream)), "exact_ctx_get_stats")
+        return {k: getattr(st, k) for k, _ in CycleStats._fields_}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -610,6 +636,9 @@ class Hybrid:
             pass
 
 
+CKPT_MAGIC = b"EXMLPCK1"
+
+
 class MLP:
     """Proposal network on the tensor cores (see exact_mlp_* in the C header).
     Parameters are exchanged as one packed float32 vector
@@ -648,6 +677,56 @@ class MLP:
         a = np.empty(self.num_params, dtype=np.float32)
         _check(load().exact_mlp_get_params(self._h, a.ctypes.data), "exact_mlp_get_params")
         return a
+
+    def get_state(self):
+        """(params, Adam first moments, Adam second moments, Adam step)."""
+        import numpy as np
+        w, m, v = (np.empty(self.num_params, dtype=np.float32) for _ in range(3))
+        t = ctypes.c_longlong()
+        _check(load().exact_mlp_get_state(self._h, w.ctypes.data, m.ctypes.data, v.ctypes.data, ctypes.byref(t)),
+               "exact_mlp_get_state")
+        return w, m, v, int(t.value)
+
+    def set_state(self, w, m, v, step: int):
+        import numpy as np
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(-1)) for a in (w, m, v)]
+        if any(a.size != self.num_params for a in arrs):
+            raise ValueError(f"expected {self.num_params} values per array")
+        _check(load().exact_mlp_set_state(self._h, arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data,
+                                          int(step)), "exact_mlp_set_state")
+
+    def save_checkpoint(self, path: str):
+        """Flat binary checkpoint: a 64-byte header (CKPT_MAGIC, format
+        version, d_in, hidden, d_out, number of parameters, Adam step, all
+        little-endian), then the parameters, Adam's first and second moments
+        (float32 each, packed like the parameter vector)."""
+        import struct
+        w, m, v, t = self.get_state()
+        head = struct.pack("<8sIIIIqq", CKPT_MAGIC, 1, self.d_in, self.hidden, self.d_out, self.num_params, t)
+        tmp = path + ".tmp"
+        with open(tmp, "wb") as fh:
+            fh.write(head.ljust(64, b"\0"))
+            for a in (w, m, v):
+                fh.write(a.astype("<f4").tobytes())
+        os.replace(tmp, path)
+
+    def load_checkpoint(self, path: str):
+        """Restore a checkpoint written by save_checkpoint for this shape."""
+        import struct
+
+        import numpy as np
+        with open(path, "rb") as fh:
+            head = fh.read(64)
+            magic, ver, d_in, hidden, d_out, n, t = struct.unpack("<8sIIIIqq", head[:40])
+            if magic != CKPT_MAGIC or ver != 1:
+                raise ValueError(f"{path}: not a proposal-network checkpoint")
+            if (d_in, hidden, d_out, n) != (self.d_in, self.hidden, self.d_out, self.num_params):
+                raise ValueError(f"{path}: shape {(d_in, hidden, d_out)} does not match "
+                                 f"{(self.d_in, self.hidden, self.d_out)}")
+            data = np.frombuffer(fh.read(12 * n), dtype="<f4")
+        if data.size != 3 * n:
+            raise ValueError(f"{path}: truncated")
+        self.set_state(data[:n], data[n:2 * n], data[2 * n:], t)
 
     def unpack(self, flat):
         out, k = [], 0

@@ -30,6 +30,8 @@ struct exact_ctx {
     size_t scratch_bytes = 0;
     int *d_err = nullptr;        // device error word (exact_status)
     long long mppi_layout = -1;  // (K, T, parts) of the last mppi_step; -1 = arena reused otherwise
+    bool stats = false;          // mppi_step also records cycle statistics
+    exact_cycle_stats *d_stats = nullptr;   // device record of those statistics
 };
 
 namespace exact {

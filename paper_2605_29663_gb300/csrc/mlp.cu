@@ -365,6 +365,37 @@ extern "C" int exact_mlp_get_params(const exact_mlp *m, float *host_params) {
     return cuda_status(cudaMemcpy(host_params, m->w, (size_t)m->nparam * 4, cudaMemcpyDeviceToHost));
 }
 
+extern "C" int exact_mlp_get_state(const exact_mlp *m, float *host_params, float *host_m, float *host_v,
+                                   long long *step) {
+    if (!m || !host_params || !host_m || !host_v || !step) return EXACT_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return EXACT_ECUDA;
+    const size_t bytes = (size_t)m->nparam * 4;
+    if (cudaMemcpy(host_params, m->w, bytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(host_m, m->m, bytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(host_v, m->v, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return EXACT_ECUDA;
+    *step = m->t;
+    return EXACT_OK;
+}
+
+extern "C" int exact_mlp_set_state(exact_mlp *m, const float *host_params, const float *host_m, const float *host_v,
+                                   long long step) {
+    if (!m || !host_params || !host_m || !host_v || step < 0 || step > (1ll << 30)) return EXACT_EINVAL;
+    for (long long k = 0; k < m->nparam; ++k)
+        if (!isfinite(host_params[k]) || !isfinite(host_m[k]) || !(host_v[k] >= 0.f) || !isfinite(host_v[k]))
+            return EXACT_EINVAL;
+    const size_t bytes = (size_t)m->nparam * 4;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(m->w, host_params, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->m, host_m, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->v, host_v, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        return EXACT_ECUDA;
+    m->t = (int)step;
+    const int rc = refresh_bf16(m, 0);
+    if (rc != EXACT_OK) return rc;
+    return cuda_status(cudaDeviceSynchronize());
+}
+
 extern "C" int exact_mlp_forward(exact_mlp *m, const float *x, int B, float *y, void *stream) {
     if (!m || !x || !y || B < 0) return EXACT_EINVAL;
     if (B == 0) return EXACT_OK;

@@ -28,6 +28,46 @@
 
 namespace exact {
 
+// Statistics of the cycle just run (one block, after the validation): the
+// normalised weights' effective sample size, J~ minimum and mean, and the
+// validation outcome (the flag the validation blocks left in the header).
+__global__ void __launch_bounds__(256)
+cycle_stats_kernel(const double *__restrict__ Jt, const float *__restrict__ wt, int K, const ArenaHeader *hdr,
+                   exact_cycle_stats *stats) {
+    __shared__ double s[4][8];
+    double z = 0.0, z2 = 0.0, jsum = 0.0, jmin = 1.0e308;
+    for (int r = threadIdx.x; r < K; r += blockDim.x) {
+        const double w = wt[r], j = Jt[r];
+        z += w;
+        z2 += w * w;
+        jsum += j;
+        jmin = fmin(jmin, j);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        z += __shfl_xor_sync(0xffffffffu, z, o);
+        z2 += __shfl_xor_sync(0xffffffffu, z2, o);
+        jsum += __shfl_xor_sync(0xffffffffu, jsum, o);
+        jmin = fmin(jmin, __shfl_xor_sync(0xffffffffu, jmin, o));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s[0][w] = z; s[1][w] = z2; s[2][w] = jsum; s[3][w] = jmin; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        z = s[0][0]; z2 = s[1][0]; jsum = s[2][0]; jmin = s[3][0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            z += s[0][k]; z2 += s[1][k]; jsum += s[2][k]; jmin = fmin(jmin, s[3][k]);
+        }
+        const int bad = *(volatile const int *)&hdr->bad;
+        stats->cycles += 1;
+        stats->validation_failures += bad ? 1 : 0;
+        stats->ess = (float)(z * z / z2);
+        stats->cost_min = (float)jmin;
+        stats->cost_mean = (float)(jsum / K);
+        stats->last_valid = bad ? 0 : 1;
+    }
+}
+
 static int parts_of(const exact_ctx *ctx, int K, int T) {
     return parts_for(K, T, ctx->sm_count > 0 ? ctx->sm_count : 148);
 }
@@ -136,7 +176,10 @@ int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const
         V.mask = nullptr;
         cc = circ;
     }
-    return launch_cycle(V, fp, st, sort, cc, ctx->sm_count > 0 ? ctx->sm_count : current_sm_count());
+    rc = launch_cycle(V, fp, st, sort, cc, ctx->sm_count > 0 ? ctx->sm_count : current_sm_count());
+    if (rc != EXACT_OK || !ctx->stats) return rc;
+    cycle_stats_kernel<<<1, 256, 0, st>>>(V.Jt, V.wt, P.K, V.hdr, ctx->d_stats);
+    return cuda_status(cudaGetLastError());
 }
 
 // Clouds with point velocities go to mppi_predicted.cu.  Static clouds go to

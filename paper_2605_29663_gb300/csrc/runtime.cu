@@ -225,8 +225,15 @@ extern "C" int exact_ctx_create(exact_ctx **out) {
     if (cudaGetDevice(&ctx->device) != cudaSuccess) { delete ctx; return EXACT_ECUDA; }
     ctx->sm_count = exact::current_sm_count();
     if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess) { delete ctx; return EXACT_ECUDA; }
-    if (cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&ctx->d_stats, sizeof(exact_cycle_stats)) != cudaSuccess) {
         cudaFree(ctx->d_err);
+        delete ctx;
+        return EXACT_ECUDA;
+    }
+    if (cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_stats, 0, sizeof(exact_cycle_stats)) != cudaSuccess) {
+        cudaFree(ctx->d_err);
+        cudaFree(ctx->d_stats);
         delete ctx;
         return EXACT_ECUDA;
     }
@@ -239,7 +246,25 @@ extern "C" void exact_ctx_destroy(exact_ctx *ctx) {
     cudaDeviceSynchronize();
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_stats) cudaFree(ctx->d_stats);
     delete ctx;
+}
+
+extern "C" int exact_ctx_enable_stats(exact_ctx *ctx, int enable) {
+    if (!ctx) return EXACT_EINVAL;
+    ctx->stats = enable != 0;
+    return EXACT_OK;
+}
+
+extern "C" int exact_ctx_get_stats(exact_ctx *ctx, exact_cycle_stats *out, void *stream) {
+    if (!ctx || !out) return EXACT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    // read, then zero the two counters (the first 16 bytes), in stream order
+    if (cudaMemcpyAsync(out, ctx->d_stats, sizeof(exact_cycle_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_stats, 0, 2 * sizeof(long long), st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return EXACT_ECUDA;
+    return EXACT_OK;
 }
 
 extern "C" int exact_ctx_get_error(exact_ctx *ctx, void *stream) {

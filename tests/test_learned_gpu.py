@@ -188,3 +188,33 @@ def test_trained_proposal_gains_over_plain(ex):
     assert prop["proposal_chosen_frac"] > base["proposal_chosen_frac"]
     assert prop["best_cost_gain_mean"] > base["best_cost_gain_mean"]
     assert diff.mean() < ci
+
+
+def test_checkpoint_resume_is_bitwise(ex, tmp_path):
+    """Training k Adam steps, saving the flat checkpoint (parameters, both
+    moments, step count), and training k more gives the same losses and
+    parameters, bit for bit, as a fresh network restored from the checkpoint
+    and trained the same k steps."""
+    g = np.random.default_rng(21)
+    D, H, O, B, k = 40, 128, 12, 512, 6
+    xs = [_t(g.normal(size=(B, D))) for _ in range(2 * k)]
+    ts = [_t(np.tanh(g.normal(size=(B, O)))) for _ in range(2 * k)]
+    a = ex.MLP(D, H, O, B)
+    a.init_params(seed=9)
+    for i in range(k):
+        a.train_step(xs[i], ts[i], 2e-3)
+    path = str(tmp_path / "proposal.ckpt")
+    a.save_checkpoint(path)
+    la = [a.train_step(xs[i], ts[i], 2e-3).item() for i in range(k, 2 * k)]
+    b = ex.MLP(D, H, O, B)
+    b.init_params(seed=1)                    # different start: everything comes from the checkpoint
+    b.load_checkpoint(path)
+    lb = [b.train_step(xs[i], ts[i], 2e-3).item() for i in range(k, 2 * k)]
+    assert la == lb
+    wa, ma, va, sa = a.get_state()
+    wb, mb, vb, sb = b.get_state()
+    assert sa == sb == 2 * k
+    for x, y in ((wa, wb), (ma, mb), (va, vb)):
+        np.testing.assert_array_equal(x, y)
+    with pytest.raises(ValueError):
+        ex.MLP(D, H + 1, O, B).load_checkpoint(path)

@@ -363,3 +363,34 @@ def test_point_pruning_small_clouds(ex, ctx, K, T, N, kind, masked):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
     assert a["valid"] == b["valid"]
     compare(s, b, o, check_dmin=False)
+
+
+def test_cycle_statistics_match_the_oracle(ex):
+    """exact_ctx_get_stats after cycles with statistics enabled: ESS =
+    1 / sum omega^2 and the minimum of J~ from the oracle's weights and costs,
+    the mean of J~ from the GPU's own costs, and the cycle and
+    validation-failure counters (a cycle forced to fail validation counts)."""
+    import torch
+    sctx = ex.Context()
+    sctx.enable_stats()
+    s, o = _seeded(lambda k: synth.plain_step(k), 90)
+    g = run_gpu(ex, sctx, s)
+    st = sctx.get_stats()
+    assert st["cycles"] == 1 and st["validation_failures"] == 0 and st["last_valid"] == int(o["valid"])
+    ess = 1.0 / np.sum(o["weights"] ** 2)
+    assert abs(st["ess"] - ess) <= 1e-4 * ess
+    assert abs(st["cost_min"] - o["costs"].min()) <= 1e-5 * abs(o["costs"].min()) + 1e-3
+    assert abs(st["cost_mean"] - g["costs"].astype(np.float64).mean()) <= 1e-5 * abs(g["costs"].mean()) + 1e-3
+    # a failing cycle (obstacle inside the footprint near the start), then a good one
+    bad = synth.plain_step(0, K=32, T=8, N=64)
+    bad["cloud"][0] = (0.0, 0.0)
+    bad["U"] = np.tile([0.2, 0.0], (8, 1)).astype(np.float32)
+    run_gpu(ex, sctx, bad)
+    run_gpu(ex, sctx, s)
+    st = sctx.get_stats()
+    assert st["cycles"] == 2 and st["validation_failures"] == 1 and st["last_valid"] == int(o["valid"])
+    assert sctx.get_stats()["cycles"] == 0          # the read zeroed the counters
+    sctx.enable_stats(False)
+    run_gpu(ex, sctx, s)
+    torch.cuda.synchronize()
+    assert sctx.get_stats()["cycles"] == 0
