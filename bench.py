@@ -578,6 +578,38 @@ def batched_small_extra(torch, ex, dev, n_scenes=128, steps=5):
     return out
 
 
+def learned_extra(torch, ex, dev, samples=20000, episodes=32, max_steps=150):
+    """The learned sampling proposal at reduced scale: closed-loop plain MPPI
+    (K = 4096) data in 64 guided worlds, a few epochs of training on the
+    tensor-core MLP kernels, then held-out worlds (the same for every method)
+    with plain K = 4096, plain K = 256 and the proposal at K = 256 (plain
+    fallback on the same noise); final trajectory costs paired per world."""
+    import numpy as np
+    from paper_2605_29663_gb300 import learned as L
+    t0 = time.time()
+    X, Y = L.generate_dataset(torch, dev, samples, 64, 4096, seed=0, log=None)
+    t_data = time.time() - t0
+    mlp = ex.MLP(L.D_IN, 256, 2 * L.T_H, 1024)
+    mlp.init_params(0)
+    t0 = time.time()
+    hist = L.train(torch, mlp, X, Y, epochs=4, batch=1024, lr=1e-3, seed=0, log=None)
+    t_train = time.time() - t0
+    kw = dict(max_steps=max_steps, log=None)
+    res = {"plain_K4096": L.evaluate(torch, dev, "plain", 4096, episodes, 10_000, **kw),
+           "plain_K256": L.evaluate(torch, dev, "plain", 256, episodes, 10_000, **kw),
+           "proposal_K256": L.evaluate(torch, dev, "proposal", 256, episodes, 10_000, mlp=mlp, **kw)}
+    out = {"samples": samples, "episodes": episodes, "max_steps": max_steps, "data_s": t_data, "train_s": t_train,
+           "val_loss": [h["val_loss"] for h in hist]}
+    for k, r in res.items():
+        out[k] = {"cost_mean": r["cost_mean"], "cost_ci95": r["cost_ci95"], "success_rate": r["success_rate"],
+                  "collision_rate": r["collision_rate"], "gpu_ms_per_step": r["gpu_ms_per_step"]}
+    out["proposal_K256"]["kept_frac"] = res["proposal_K256"].get("proposal_chosen_frac")
+    for a, b in (("proposal_K256", "plain_K4096"), ("proposal_K256", "plain_K256"), ("plain_K4096", "plain_K256")):
+        d = np.array(res[a]["costs"]) - np.array(res[b]["costs"])
+        out[f"paired_{a}_minus_{b}"] = {"mean": float(d.mean()), "ci95": float(1.96 * d.std(ddof=1) / math.sqrt(d.size))}
+    return out
+
+
 def run_mppi_workload(args):
     """Time one MPPI cycle workload on its own, as plain launches (for
     profiling): plain_step, forklift, predicted (the dynamic scene through
@@ -662,6 +694,12 @@ def mppi_summary(extra: dict) -> dict:
     if p:
         out["predicted_K1024_T20_N2048"] = {"us_per_step": round(p["predicted_us_per_step"], 2),
                                             "static_us_per_step": round(p["static_us_per_step"], 2)}
+    lr = extra.get("learned")
+    if lr:
+        out["learned_reduced"] = {k: round(lr[k]["cost_mean"], 1) for k in ("plain_K4096", "plain_K256", "proposal_K256")}
+        out["learned_reduced"]["paired_proposal_minus_plain4096"] = [
+            round(lr["paired_proposal_K256_minus_plain_K4096"]["mean"], 1),
+            round(lr["paired_proposal_K256_minus_plain_K4096"]["ci95"], 1)]
     for key in ("batched64", "batched_small128"):
         b = extra.get(key)
         if b:
@@ -860,6 +898,7 @@ def run_gpu(args):
         line["extra"]["hybrid3"] = hybrid_extra(torch, ex, dev, cpu=not args.no_cpu)
         line["extra"]["predicted"] = predicted_extra(torch, ex, dev, cpu=not args.no_cpu)
         line["extra"].update(sdf_extra(torch, ex, dev))
+        line["extra"]["learned"] = learned_extra(torch, ex, dev)
         line["mppi"] = mppi_summary(line["extra"])   # last key: short enough to survive a truncated tail
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -21,6 +21,13 @@ the arena, starting at least 2.5 m from the robot), all sampled as points
 every 0.05 m; the robot senses the points within 6 m, fitted to a budget of
 N = 2048 (uniform subsample, or zero padding plus mask).  An episode ends at
 the goal (0.5 m), at a collision (exact clearance < 0) or after 250 steps.
+
+Guidance (the upstream module the paper assumes): at every reset a shortest
+path from start to goal around the static boxes is planned on a 0.25 m grid
+(8-connected, cells within 0.8 m of a box blocked); each cycle MPPI's goal
+point is the point of that path LOOKAHEAD metres ahead of the path point
+nearest the robot (the final goal near the end).  The discs are not planned
+around: the local controller has to avoid them.
 """
 from __future__ import annotations
 
@@ -47,6 +54,63 @@ SIGMA = (0.3, 0.6)
 U_LO, U_HI = (-1.0, -1.5), (1.5, 1.5)
 GOAL_TOL = 0.5
 D_IN = NBINS + 7 + 2 * T_H          # 111
+GRID = 0.25                          # m, guidance planning grid
+INFLATE = 0.8                        # m, blocked margin around boxes
+LOOKAHEAD = 3.0                      # m along the planned path
+
+
+def plan_path(boxes: list, start, goal, lo, hi) -> np.ndarray:
+    """Shortest 8-connected grid path (cell centres, start to goal) that keeps
+    INFLATE metres from every box (cx, cy, w, h); the straight segment when no
+    path exists."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import dijkstra
+    nx, ny = int(math.ceil((hi[0] - lo[0]) / GRID)), int(math.ceil((hi[1] - lo[1]) / GRID))
+    xs = lo[0] + (np.arange(nx) + 0.5) * GRID
+    ys = lo[1] + (np.arange(ny) + 0.5) * GRID
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    free = np.ones((nx, ny), bool)
+    for cx, cy, w, h in boxes:
+        dx = np.maximum(np.abs(X - cx) - w / 2, 0.0)
+        dy = np.maximum(np.abs(Y - cy) - h / 2, 0.0)
+        free &= np.hypot(dx, dy) > INFLATE
+    cell = lambda p: (min(nx - 1, max(0, int((p[0] - lo[0]) / GRID))), min(ny - 1, max(0, int((p[1] - lo[1]) / GRID))))
+    s, gcell = cell(start), cell(goal)
+    free[s] = free[gcell] = True
+    idx = np.arange(nx * ny).reshape(nx, ny)
+    rows, cols, wts = [], [], []
+    for di, dj in ((1, 0), (0, 1), (1, 1), (1, -1)):
+        a = idx[max(0, -di):nx - max(0, di), max(0, -dj):ny - max(0, dj)]
+        b = idx[max(0, di):nx - max(0, -di) if di <= 0 else nx, max(0, dj):ny if dj >= 0 else ny + dj]
+        a, b = a.ravel(), b.ravel()
+        ok = free.ravel()[a] & free.ravel()[b]
+        rows.append(a[ok]); cols.append(b[ok]); wts.append(np.full(ok.sum(), math.hypot(di, dj)))
+    r, c, w = np.concatenate(rows), np.concatenate(cols), np.concatenate(wts)
+    G = csr_matrix((np.concatenate([w, w]), (np.concatenate([r, c]), np.concatenate([c, r]))), shape=(nx * ny,) * 2)
+    _, pred = dijkstra(G, indices=idx[gcell], return_predecessors=True)
+    k = idx[s]
+    if k != idx[gcell] and pred[k] < 0:
+        return np.array([start, goal], float)
+    path = [start]
+    while k != idx[gcell] and k >= 0:
+        k = pred[k]
+        path.append((xs[k // ny], ys[k % ny]))
+    path.append(goal)
+    return np.array(path, float)
+
+
+def lookahead_point(path: np.ndarray, pos) -> np.ndarray:
+    """The point LOOKAHEAD metres along `path` beyond its vertex nearest to pos."""
+    k = int(np.argmin(np.hypot(path[:, 0] - pos[0], path[:, 1] - pos[1])))
+    left = LOOKAHEAD
+    while k + 1 < len(path):
+        seg = path[k + 1] - path[k]
+        L = math.hypot(*seg)
+        if L >= left:
+            return path[k] + seg * (left / L)
+        left -= L
+        k += 1
+    return path[-1]
 
 
 def mppi_params(K: int) -> dict:
@@ -68,6 +132,7 @@ class World:
         self.prev_cmd = np.zeros((n, 2))
         self.steps = np.zeros(n, dtype=int)
         self.static = [None] * n
+        self.path = [None] * n
         self.dc = np.zeros((n, n_discs, 2))
         self.dv = np.zeros((n, n_discs, 2))
         self.lo = np.zeros((n, 2))
@@ -87,14 +152,16 @@ class World:
         self.steps[i] = 0
         self.lo[i] = (-12.0, -15.0)
         self.hi[i] = (G + 12.0, 15.0)
-        boxes = []
+        boxes, rects = [], []
         while len(boxes) < self.n_boxes:
             c = np.array([g.uniform(2.0, G - 0.5), g.uniform(-6.0, 6.0)])
             if np.hypot(*c) < 2.0 or np.hypot(*(c - self.goal[i])) < 1.5:
                 continue
             w, h = g.uniform(0.3, 1.0, 2)
             boxes.append(synth.box_edge_points(c[0], c[1], w, h, 0.05))
+            rects.append((c[0], c[1], w, h))
         self.static[i] = np.concatenate(boxes) if boxes else np.zeros((0, 2))
+        self.path[i] = plan_path(rects, (0.0, 0.0), tuple(self.goal[i]), (-4.0, -9.0), (G + 4.0, 9.0))
         k = 0
         while k < self.n_discs:
             c = g.uniform(self.lo[i], self.hi[i])
@@ -134,6 +201,10 @@ class World:
 
     def goal_dist(self) -> np.ndarray:
         return np.hypot(self.pose[:, 0] - self.goal[:, 0], self.pose[:, 1] - self.goal[:, 1])
+
+    def guidance(self) -> np.ndarray:
+        """Each robot's goal point for this cycle: LOOKAHEAD metres ahead on its planned path."""
+        return np.stack([lookahead_point(self.path[i], self.pose[i, :2]) for i in range(self.n)])
 
 
 def executed_clearance(world: World, fp: Footprint, torch, dev) -> np.ndarray:
@@ -185,7 +256,7 @@ class PlainController:
         S.state.copy_(t.from_numpy(world.pose.astype(np.float32)))
         S.cloud.copy_(t.from_numpy(cl))
         S.mask.copy_(t.from_numpy(mk))
-        S.goal.copy_(t.from_numpy(world.goal.astype(np.float32))[:, None, :])
+        S.goal.copy_(t.from_numpy(world.guidance().astype(np.float32))[:, None, :])
 
     def reset_env(self, i: int):
         self.S.U[i].zero_()
@@ -222,11 +293,12 @@ class ProposalController:
 
     def step(self, world: World, cl, mk, gen):
         t = self.torch
+        goal = t.from_numpy(world.guidance().astype(np.float32))[:, None, :]
         for S in (self.P, self.Q):
             S.state.copy_(t.from_numpy(world.pose.astype(np.float32)))
             S.cloud.copy_(t.from_numpy(cl))
             S.mask.copy_(t.from_numpy(mk))
-            S.goal.copy_(t.from_numpy(world.goal.astype(np.float32))[:, None, :])
+            S.goal.copy_(goal)
         self.prev_cmd.copy_(t.from_numpy(world.prev_cmd.astype(np.float32)))
         polar_hist(self.P.cloud, self.P.state, NBINS, R_MAX, masks=self.P.mask, out=self.hist)
         proposal_features(self.hist, self.P.state, self.P.goal[:, 0, :].contiguous(), self.prev_cmd, self.U_prev,
@@ -424,8 +496,7 @@ def main(argv=None):
     os.makedirs(os.path.dirname(a.out) or ".", exist_ok=True)
     with open(a.out, "w") as f:
         json.dump(out, f)
-    params = mlp.get_params()
-    np.save(os.path.splitext(a.out)[0] + "_params.npy", params)
+    mlp.save_checkpoint(os.path.splitext(a.out)[0] + ".ckpt")   # parameters, Adam moments and step
     print(json.dumps(out["evaluation"]))
 
 
