@@ -50,7 +50,7 @@ L2_BYTES = 129 * 1024 * 1024
 # null otherwise).
 TRAFFIC = {"sources": ["paper_2605_29663_gb300/csrc/sdf_batch.cu", "paper_2605_29663_gb300/csrc/common.cuh",
                        "paper_2605_29663_gb300/csrc/internal.h"],
-           "sha256_16": "d71e18adb593d732", "bytes_per_launch": 406784 + 478232576}
+           "sha256_16": "0e27f48e057d4b4a", "bytes_per_launch": 709888 + 477858304}
 
 
 def measured_traffic():
@@ -613,7 +613,8 @@ def learned_extra(torch, ex, dev, samples=20000, episodes=32, max_steps=150):
 def run_mppi_workload(args):
     """Time one MPPI cycle workload on its own, as plain launches (for
     profiling): plain_step, forklift, predicted (the dynamic scene through
-    mppi_step_predicted), hybrid (three modes) or batched64."""
+    mppi_step_predicted), hybrid (three modes), batched64, or mlp_train (one
+    training step of the proposal network)."""
     import torch
 
     import paper_2605_29663_gb300 as ex
@@ -651,6 +652,22 @@ def run_mppi_workload(args):
         step = h.step
         launches = 4
         cfg = {"modes": 3, "K": modes[0]["params"]["K"], "T": modes[0]["params"]["T"], "N": modes[0]["cloud"].shape[0]}
+    elif args.workload == "mlp_train":
+        # one Adam step of the proposal network (111-256-256-40, batch 1024)
+        # on the tensor-core kernels, seeded synthetic inputs and targets
+        import numpy as np
+        from paper_2605_29663_gb300 import learned as L
+        g = np.random.default_rng(0)
+        x = torch.from_numpy(g.normal(size=(1024, L.D_IN)).astype(np.float32)).to(dev)
+        y = torch.from_numpy((0.1 * g.normal(size=(1024, 2 * L.T_H))).astype(np.float32)).to(dev)
+        net = ex.MLP(L.D_IN, 256, 2 * L.T_H, 1024)
+        net.init_params(0)
+        loss = torch.empty(1, device=dev)
+
+        def step():
+            net.train_step(x, y, 1e-3, loss=loss)
+        launches = 16
+        cfg = {"network": f"{L.D_IN}-256-256-{2 * L.T_H}", "batch": 1024}
     else:
         scenes = synth.batched(0)
         devs = [dict(state=torch.from_numpy(s["q0"]).to(dev), cloud=torch.from_numpy(s["cloud"]).to(dev),
@@ -671,7 +688,8 @@ def run_mppi_workload(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"metric": "MPPI steps/s", "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1,
+    metric = "proposal-network training steps/s" if args.workload == "mlp_train" else "MPPI steps/s"
+    print(json.dumps({"metric": metric, "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                       "config": dict({"workload": args.workload}, **cfg),
@@ -917,7 +935,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target length of the CPU oracle sample")
     ap.add_argument("--sdf-poses", type=int, default=N_POSES,
                     help="poses of the sdf workload (fewer only to profile a small case)")
-    ap.add_argument("--workload", choices=["sdf", "plain_step", "forklift", "predicted", "hybrid", "batched64"],
+    ap.add_argument("--workload", choices=["sdf", "plain_step", "forklift", "predicted", "hybrid", "batched64",
+                                           "mlp_train"],
                     default="sdf",
                     help="sdf (headline) or one MPPI cycle workload timed on its own")
     args = ap.parse_args()

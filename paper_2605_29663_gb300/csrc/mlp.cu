@@ -11,11 +11,14 @@
 // One generic tiled GEMM serves all products through strided operand views
 // (C[i][j] = sum_k A(i,k) B(k,j), A(i,k) = A[i sar + k sac]), so forward
 // (X W^T), input gradients (dZ W) and weight gradients (dZ^T H) are the same
-// kernel with different strides and epilogues.
+// kernel with different strides and epilogues.  Weight gradients reduce over
+// the batch (K = B) into few output tiles; they are split along K over
+// gridDim.z into FP32 partial tiles, added in a fixed order afterwards.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -44,6 +47,8 @@ struct GemmArgs {
     const float *gz;   // pre-activation for EPI_GELU_GRAD (row-major, ldgz)
     int ldgz;
     int epi;
+    int kchunk;        // k range of one block along gridDim.z (split-K); K when unsplit
+    float *P;          // split-K: FP32 partial tiles P[z][i][j] (M x N each), summed by splitk_sum_kernel
 };
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
@@ -81,14 +86,15 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
 
-    for (int k0 = 0; k0 < g.K; k0 += GK) {
+    const int kb = blockIdx.z * g.kchunk, ke = min(g.K, kb + g.kchunk);
+    for (int k0 = kb; k0 < ke; k0 += GK) {
         for (int e = threadIdx.x; e < GM * GK; e += 128) {
             const int r = e / GK, c = e - r * GK, i = i0 + r, k = k0 + c;
-            As[r][c] = (i < g.M && k < g.K) ? g.A[(long long)i * g.sar + (long long)k * g.sac] : zero;
+            As[r][c] = (i < g.M && k < ke) ? g.A[(long long)i * g.sar + (long long)k * g.sac] : zero;
         }
         for (int e = threadIdx.x; e < GN * GK; e += 128) {
             const int r = e / GK, c = e - r * GK, j = j0 + r, k = k0 + c;
-            Bs[r][c] = (j < g.N && k < g.K) ? g.B[(long long)k * g.sbr + (long long)j * g.sbc] : zero;
+            Bs[r][c] = (j < g.N && k < ke) ? g.B[(long long)k * g.sbr + (long long)j * g.sbc] : zero;
         }
         __syncthreads();
 #pragma unroll
@@ -128,6 +134,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
                     const int j = j0 + wn * 32 + ni * 8 + 2 * t4 + c;
                     if (i >= g.M || j >= g.N) continue;
                     float v = acc[mi][ni][2 * h + c];
+                    if (g.P) {   // split-K: this block's partial, no epilogue
+                        g.P[((long long)blockIdx.z * g.M + i) * g.N + j] = v;
+                        continue;
+                    }
                     float out = v;
                     if (g.epi == EPI_BIAS || g.epi == EPI_BIAS_GELU) v += g.bias[j];
                     if (g.epi == EPI_BIAS_GELU) {
@@ -142,6 +152,17 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
                     }
                     if (g.C) g.C[(long long)i * g.ldc + j] = out;
                 }
+}
+
+// C[i][j] (row stride ldc) = sum_z P[z][i][j], z in order (fixed, so the
+// result does not depend on scheduling)
+__global__ void splitk_sum_kernel(const float *__restrict__ P, int S, int M, int N, float *__restrict__ C, int ldc) {
+    const long long n = (long long)M * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        float a = 0.f;
+        for (int z = 0; z < S; ++z) a += P[z * n + e];
+        C[(e / N) * ldc + e % N] = a;
+    }
 }
 
 // x (B x d_in, FP32) -> Xb (B x 128, BF16, zero-padded)
@@ -180,12 +201,22 @@ mse_grad_kernel(const float *__restrict__ Y, const float *__restrict__ tgt, int 
     }
 }
 
-// g[j] = sum_b D[b][j]  (bias gradients; one thread per column, fixed order)
-__global__ void colsum_kernel(const float *__restrict__ D, int B, int n, float *__restrict__ g) {
+// Bias gradients g[j] = sum_b D[b][j] in two fixed-order stages: slice s of
+// kColSlices adds its rows b = s, s + kColSlices, ... (one thread per column,
+// coalesced across columns), then colsum_finish adds the slices in order.
+constexpr int kColSlices = 32;
+__global__ void colsum_kernel(const float *__restrict__ D, int B, int n, float *__restrict__ part) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, sl = blockIdx.y;
+    if (j >= n) return;
+    float a = 0.f;
+    for (int b = sl; b < B; b += kColSlices) a += D[(long long)b * n + j];
+    part[(long long)sl * n + j] = a;
+}
+__global__ void colsum_finish_kernel(const float *__restrict__ part, int n, float *__restrict__ g) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     float a = 0.f;
-    for (int b = 0; b < B; ++b) a += D[(long long)b * n + j];
+    for (int sl = 0; sl < kColSlices; ++sl) a += part[(long long)sl * n + j];
     g[j] = a;
 }
 
@@ -226,18 +257,44 @@ struct exact_mlp {
     bf16 *W1b, *W2b, *W3b;                    // BF16 weights (W1b rows padded to 128)
     bf16 *Xb, *H1b, *H2b, *dYb, *dZb;         // BF16 operands
     float *Z1, *Z2, *Y, *dY, *dZ, *loss;      // FP32 activations / gradients
+    float *ws;                                // split-K partial tiles and column-sum slices
     int t = 0;                                // Adam step
 };
+
+// split-K factor of a GEMM whose output tiles would not fill the GPU
+constexpr int kSplitMax = 16;
+static int splits_for(int M, int N, int K) {
+    const int tiles = ((M + GM - 1) / GM) * ((N + GN - 1) / GN);
+    int s = 1;
+    while (s < kSplitMax && tiles * s * 2 <= 152 && K / (s * 2) >= 2 * GK) s *= 2;
+    return s;
+}
 
 static int grid_for(long long n, int block) {
     long long g = (n + block - 1) / block;
     return (int)(g < 1 ? 1 : (g > 65535 ? 65535 : g));
 }
 
-static cudaError_t gemm(const GemmArgs &g, cudaStream_t st) {
-    dim3 grid((g.N + GN - 1) / GN, (g.M + GM - 1) / GM);
+static cudaError_t gemm(const GemmArgs &g0, cudaStream_t st, float *ws = nullptr) {
+    GemmArgs g = g0;
+    // weight gradients (no epilogue, K = the batch) are split along K into
+    // partial tiles when their output tiles alone would not fill the GPU
+    const int S = (ws && g.epi == EPI_PLAIN && !g.Cb) ? splits_for(g.M, g.N, g.K) : 1;
+    g.kchunk = S > 1 ? ((g.K + S - 1) / S + GK - 1) / GK * GK : g.K;
+    g.P = S > 1 ? ws : nullptr;
+    dim3 grid((g.N + GN - 1) / GN, (g.M + GM - 1) / GM, S);
     gemm_bf16_kernel<<<grid, 128, 0, st>>>(g);
+    if (S > 1) {
+        const long long n = (long long)g.M * g.N;
+        splitk_sum_kernel<<<(int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(ws, S, g.M, g.N, g.C,
+                                                                                               g.ldc);
+    }
     return cudaGetLastError();
+}
+
+static void colsum(const float *D, int B, int n, float *g, float *ws, cudaStream_t st) {
+    colsum_kernel<<<dim3((n + 127) / 128, kColSlices), 128, 0, st>>>(D, B, n, ws);
+    colsum_finish_kernel<<<(n + 127) / 128, 128, 0, st>>>(ws, n, g);
 }
 
 static GemmArgs make_gemm(int M, int N, int K, const bf16 *A, long long sar, long long sac, const bf16 *B, long long sbr,
@@ -281,22 +338,22 @@ static int backward(exact_mlp *m, const float *x, const float *target, int B, cu
     mse_grad_kernel<<<1, 1024, 0, st>>>(m->Y, target, B, O, m->dY, m->dYb, m->loss);
     // layer 3: gW3 = dY^T H2, gb3 = sum dY, dZ2 = (dY W3) * g'(Z2)
     GemmArgs a = make_gemm(O, H, B, m->dYb, 1, O, m->H2b, H, 1, m->g + m->oW3, H, EPI_PLAIN);
-    colsum_kernel<<<(O + 127) / 128, 128, 0, st>>>(m->dY, B, O, m->g + m->ob3);
+    colsum(m->dY, B, O, m->g + m->ob3, m->ws, st);
     GemmArgs b = make_gemm(B, H, O, m->dYb, O, 1, m->W3b, H, 1, m->dZ, H, EPI_GELU_GRAD);
     b.gz = m->Z2; b.ldgz = H; b.Cb = m->dZb; b.ldcb = H;
-    if (gemm(a, st) != cudaSuccess || gemm(b, st) != cudaSuccess) return EXACT_ECUDA;
+    if (gemm(a, st, m->ws) != cudaSuccess || gemm(b, st) != cudaSuccess) return EXACT_ECUDA;
     // layer 2: gW2 = dZ2^T H1, gb2 = sum dZ2, dZ1 = (dZ2 W2) * g'(Z1)
     GemmArgs c = make_gemm(H, H, B, m->dZb, 1, H, m->H1b, H, 1, m->g + m->oW2, H, EPI_PLAIN);
-    colsum_kernel<<<(H + 127) / 128, 128, 0, st>>>(m->dZ, B, H, m->g + m->ob2);
-    if (gemm(c, st) != cudaSuccess) return EXACT_ECUDA;
+    colsum(m->dZ, B, H, m->g + m->ob2, m->ws, st);
+    if (gemm(c, st, m->ws) != cudaSuccess) return EXACT_ECUDA;
     // dZ1 overwrites dZ / dZb only after gW2 and gb2 have consumed them (stream order)
     GemmArgs d = make_gemm(B, H, H, m->dZb, H, 1, m->W2b, H, 1, m->Z2, H, EPI_GELU_GRAD);
     d.gz = m->Z1; d.ldgz = H; d.Cb = m->H2b; d.ldcb = H;   // Z2 / H2b are free after layer 2's backward
     if (gemm(d, st) != cudaSuccess) return EXACT_ECUDA;
     // layer 1: gW1 = dZ1^T X (only the d_in real columns), gb1 = sum dZ1
     GemmArgs e = make_gemm(H, D, B, m->H2b, 1, H, m->Xb, kMlpInPad, 1, m->g + m->oW1, D, EPI_PLAIN);
-    colsum_kernel<<<(H + 127) / 128, 128, 0, st>>>(m->Z2, B, H, m->g + m->ob1);
-    if (gemm(e, st) != cudaSuccess) return EXACT_ECUDA;
+    colsum(m->Z2, B, H, m->g + m->ob1, m->ws, st);
+    if (gemm(e, st, m->ws) != cudaSuccess) return EXACT_ECUDA;
     return cuda_status(cudaGetLastError());
 }
 
@@ -318,7 +375,8 @@ extern "C" int exact_mlp_create(int d_in, int hidden, int d_out, int max_batch, 
         (size_t)(B * kMlpInPad) * 2, (size_t)(B * H) * 2, (size_t)(B * H) * 2, (size_t)(B * O) * 2,      // Xb H1b H2b dYb
         (size_t)(B * H) * 2,                                                                             // dZb
         (size_t)(B * H) * 4, (size_t)(B * H) * 4, (size_t)(B * O) * 4, (size_t)(B * O) * 4,              // Z1 Z2 Y dY
-        (size_t)(B * H) * 4, 256};                                                                       // dZ loss
+        (size_t)(B * H) * 4, 256,                                                                        // dZ loss
+        (size_t)kSplitMax * (size_t)std::max(H * std::max(H, D), O * H) * 4};                           // ws
     size_t total = 0;
     for (auto s : sz) total += align_up(s, 256);
     if (cudaMalloc(&m->dev, total) != cudaSuccess) { delete m; return EXACT_ECUDA; }
@@ -327,7 +385,7 @@ extern "C" int exact_mlp_create(int d_in, int hidden, int d_out, int max_batch, 
     void **slots[] = {(void **)&m->w, (void **)&m->g, (void **)&m->m, (void **)&m->v, (void **)&m->W1b,
                       (void **)&m->W2b, (void **)&m->W3b, (void **)&m->Xb, (void **)&m->H1b, (void **)&m->H2b,
                       (void **)&m->dYb, (void **)&m->dZb, (void **)&m->Z1, (void **)&m->Z2, (void **)&m->Y,
-                      (void **)&m->dY, (void **)&m->dZ, (void **)&m->loss};
+                      (void **)&m->dY, (void **)&m->dZ, (void **)&m->loss, (void **)&m->ws};
     for (size_t i = 0; i < sz.size(); ++i) {
         *slots[i] = p;
         p += align_up(sz[i], 256);
