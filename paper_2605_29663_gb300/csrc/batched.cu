@@ -58,7 +58,7 @@ batched_sample_kernel(const SceneDev *__restrict__ scenes, const int2 *__restric
             __syncthreads();
             fp_scene = it.x;
         }
-        const SmemEval ev{s_fp, D.kind, D.nfp, D.bc};
+        const SmemEval ev{s_fp, D.kind, D.nfp, D.bc, D.bh};
         sample_body(D.V, ev, item_sample(it), 0, sm, s_pts, it.x == pts_scene, pairs_per_lane, D.circ,
                     item_second(it));
         pts_scene = D.V.N <= kStage ? it.x : -1;
@@ -90,7 +90,7 @@ batched_validate_kernel(const SceneDev *__restrict__ scenes, const int2 *__restr
     const SceneDev &D = scenes[t.x];
     load_fp(s_fp, D);
     __syncthreads();
-    const SmemEval ev{s_fp, D.kind, D.nfp, D.bc};
+    const SmemEval ev{s_fp, D.kind, D.nfp, D.bc, D.bh};
     validate_body(D.V, ev, t.y / D.V.val_chunks, t.y % D.V.val_chunks, sm, D.circ);
 }
 
@@ -234,6 +234,7 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         D.kind = fp->kind;
         D.nfp = fp->n_pad;
         D.bc = make_float3(fp->bcx, fp->bcy, fp->brad);
+        D.bh = make_float2(fp->bhx, fp->bhy);
         if (fp->kind == EXACT_FP_POLYGON) {
             const int E = fp->n_pad;
             float *eyn = reinterpret_cast<float *>(D.fpc + 3 * E + 1);

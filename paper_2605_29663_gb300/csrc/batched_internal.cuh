@@ -17,6 +17,7 @@ struct SceneDev {
     const float4 *circ;         // sub-chunk circles of the ordered copy, or NULL
     int kind, nfp;
     float3 bc;    // footprint bounding circle
+    float2 bh;    // half extents of the footprint's bounding box about the circle's centre
     float4 fpc[kFpSlots];
 };
 

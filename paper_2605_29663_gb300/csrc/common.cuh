@@ -115,6 +115,7 @@ struct PolyC {
     f2x nkx[E];             // -e_bx / e_by     (0 when e_by == 0)
     float eyn[E];           // e_by / |e_b|^2   (scalar: its fma saturates)
     float bcx, bcy, brad;   // bounding circle: centre, radius (rounded up)
+    float bhx, bhy;         // bounding box about (bcx, bcy): half extents (rounded up)
 };
 
 // Rectangle cover (Sec. IV-B.1) padded to R boxes by repeating box 0.
@@ -123,6 +124,7 @@ struct RectC {
     f2x ncx[R], ncy[R];     // -c pairs
     float cx[R], cy[R], sx[R], sy[R];
     float bcx, bcy, brad;   // bounding circle: centre, radius (rounded up)
+    float bhx, bhy;         // bounding box about (bcx, bcy): half extents (rounded up)
 };
 
 // ---------------------------------------------------------------- transform

@@ -21,6 +21,7 @@ struct exact_footprint {
     float kx[EXACT_MAX_POLY_VERTICES];
     float cx[EXACT_MAX_RECTS], cy[EXACT_MAX_RECTS], sx[EXACT_MAX_RECTS], sy[EXACT_MAX_RECTS];
     float bcx, bcy, brad;   // bounding circle (body frame), radius rounded up
+    float bhx, bhy;         // half extents of the bounding box about (bcx, bcy), rounded up
 };
 
 struct exact_ctx {
@@ -70,6 +71,7 @@ inline PolyC<E> make_poly(const exact_footprint *fp) {
         P.nkx[b] = both(-fp->kx[b]);
     }
     P.bcx = fp->bcx; P.bcy = fp->bcy; P.brad = fp->brad;
+    P.bhx = fp->bhx; P.bhy = fp->bhy;
     return P;
 }
 
@@ -84,6 +86,7 @@ inline RectC<R> make_rect(const exact_footprint *fp) {
         Q.ncx[j] = ((unsigned long long)ux << 32) | ux; Q.ncy[j] = ((unsigned long long)uy << 32) | uy;
     }
     Q.bcx = fp->bcx; Q.bcy = fp->bcy; Q.brad = fp->brad;
+    Q.bhx = fp->bhx; Q.bhy = fp->bhy;
     return Q;
 }
 

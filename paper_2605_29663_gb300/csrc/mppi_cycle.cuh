@@ -160,7 +160,10 @@ __device__ __forceinline__ double ord2d(unsigned long long u) {
 // ---------------------------------------------------------------- evaluators
 template <class FPC>
 struct ConstEval {            // footprint constants in the kernel parameters
-    static constexpr bool kQuad = false;   // no loads to share: two points per call
+    // sub-chunk pruning tests each point against the footprint's bounding
+    // box before evaluating it: for polygons (a rectangle cover's evaluation
+    // costs about what the test does)
+    static constexpr bool kBoxTest = fp_traits<FPC>::kind == EXACT_FP_POLYGON;
     // small footprints: the unpruned loop gives each lane two pairs per
     // iteration (two independent chains; larger footprints would not fit
     // the registers)
@@ -182,6 +185,7 @@ struct ConstEval {            // footprint constants in the kernel parameters
     }
     __device__ __forceinline__ float dist(float key) const { return key_to_dist(f, key); }
     __device__ __forceinline__ float3 bound() const { return make_float3(f.bcx, f.bcy, f.brad); }
+    __device__ __forceinline__ float4 box() const { return make_float4(f.bcx, f.bcy, f.bhx, f.bhy); }
 };
 
 // Footprint constants in shared memory with a run-time edge / box count.
@@ -195,13 +199,15 @@ struct ConstEval {            // footprint constants in the kernel parameters
 __host__ __device__ constexpr int poly_slot_count(int E) { return 3 * E + 1 + (E + 3) / 4; }
 
 struct SmemEval {
-    static constexpr bool kQuad = true;   // eval4 shares each constant load among four points
+    static constexpr bool kBoxTest = true;   // footprint terms from shared memory: the test pays
     static constexpr bool kPairLoop = true;
     static constexpr bool kQueueOk = true;
     const float4 *C;
     int kind, n;
     float3 bc;    // bounding circle of the footprint (centre, radius)
+    float2 bh;    // half extents of its bounding box about the circle's centre
     __device__ __forceinline__ float3 bound() const { return bc; }
+    __device__ __forceinline__ float4 box() const { return make_float4(bc.x, bc.y, bh.x, bh.y); }
 
     // NP lane pairs of points (px[2i], px[2i+1]) against every edge / box;
     // each slot is read once for all of them.
@@ -521,25 +527,31 @@ __device__ __forceinline__ void cloud_circles(const float2 *__restrict__ pts, co
 // is the constant-velocity prediction o + t_h v at the time t_h of the scored
 // state (the time-indexed obstacle prediction of Sec. V-F).
 //
-// Schedule, in three block-wide phases:
+// Schedule when pruning (cap >= 0), in three block-wide phases:
 //  1. one lane per (step, sub-chunk): keep the pair unless the sub-chunk's
 //     circle lies farther than `cap` (plus a slack far above rounding) from
-//     the footprint's bounding circle at that step (cw) -- only when cap >= 0;
+//     the footprint's bounding circle at that step (cw);
 //  2. a prefix sum of the kept pairs per step (bit masks in msk);
-//  3. every warp evaluates an equal contiguous share of the kept (step,
-//     sub-chunk) list and folds each step's minimum into keyh[h] (one warp
-//     shuffle-min and one shared atomicMin per step run).
-// Pruning never changes a result: cap = d_safe is passed only when no d_min
-// output is wanted, and every cost term and the validation test are the same
-// for any d >= d_safe; a skipped point is provably farther than that.
-// Without pruning (cap < 0) the three phases are replaced by items (step h,
-// chunk of 128 pairs) dealt to the warps round-robin, each ending in one
-// warp shuffle-min and one shared atomicMin on the key of step h.
+//  3. every warp walks an equal contiguous share of the kept (step,
+//     sub-chunk) list; polygons and shared-memory footprints keep the points
+//     that lie within cap of the footprint's bounding box in that step's
+//     body frame and evaluate them through the warp's queue (queue:
+//     kQueueAll ints of shared memory), rectangle covers evaluate every point
+//     and fold each step's minimum into keyh[h] (one warp shuffle-min and
+//     one shared atomicMin per step run).
+// With queue_points (clouds below kPruneMin) the phases are replaced by a
+// point-level test against the footprint's bounding circle, feeding the
+// same kind of queue.  Pruning never changes a result: cap = d_safe is passed only
+// when no d_min output is wanted, and every cost term and the validation
+// test are the same for any d >= d_safe; a skipped point is provably farther
+// than that.  Without pruning (cap < 0) items (step h, chunk of 128 pairs)
+// are dealt to the warps round-robin, each ending in one warp shuffle-min and
+// one shared atomicMin on the key of step h.
 template <bool MOVING = false, class EV>
 __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose,
                                                const float4 *cw, int h0, int nh, unsigned *keyh, int ppl,
                                                const float4 *circ, float cap, unsigned *msk, int *pre,
-                                               int *queue = nullptr, int *err = nullptr) {
+                                               int *queue, bool queue_points, int *err = nullptr) {
     const int npairs = (n + 1) >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nsub = (n + kSub * ppl - 1) / (kSub * ppl);
@@ -561,7 +573,7 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
         body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
         body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
     };
-    if (cap < 0.f || (queue && !EV::kQueueOk)) {   // no pruning
+    if (cap < 0.f || (queue_points && !EV::kQueueOk)) {   // no pruning
         const int span = 32 * 4;   // pairs per item
         const int nchunk = npairs > 0 ? (npairs + span - 1) / span : 0;
         const int items = nh * nchunk;
@@ -609,7 +621,7 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
         }
         return;
     }
-    if constexpr (EV::kQueueOk) if (queue) {
+    if constexpr (EV::kQueueOk) if (queue_points) {
         // Point-level pruning (clouds below kPruneMin, no sort, no circles):
         // the warp walks its contiguous share of the (step, pair) units; each
         // lane keeps a point only if it lies within the footprint's bounding
@@ -754,55 +766,100 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
     int hh = lo;
     unsigned long long m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
     for (int k = pre[hh]; k < e0; ++k) m &= m - 1ull;
-    if constexpr (EV::kQuad) {
-        // units of one pair per lane -- (step, sub-chunk, i-th of its ppl
-        // pairs for this lane) -- in list order, two units per evaluation;
-        // each step's minimum is folded when the units move to another step
-        int e = e0, i = ppl, cs = 0, ch = 0;
-        auto next = [&](int &uh, int &uj) -> bool {
-            if (i == ppl) {
-                if (e >= e1) return false;
-                while (m == 0ull) {
+    if constexpr (EV::kBoxTest) {
+        // Polygons and shared-memory footprints: the points of a kept
+        // sub-chunk are moved into the body frame of its step and kept only
+        // if they lie within cap (plus the slack) of the footprint's bounding
+        // box there; the kept ones go through the warp's queue, as in the
+        // point-level path.  The evaluator gives the same key for that
+        // body-frame point, and sd_F >= sd_box everywhere for a footprint F
+        // inside the box, so a dropped point is provably farther than cap.
+        // (For a rectangle cover the test costs about what the evaluation
+        // does, and the kept points are evaluated directly below.)
+        const float4 fb = ev.box();
+        const int cap_q = kQueueAll / nwarps;
+        const int flush_at = cap_q >= 128 ? 64 : 1;
+        int *q = queue + warp * cap_q;
+        int qn = 0;   // warp-uniform
+        auto point_at = [&](int i, int h) -> float2 {
+            if constexpr (MOVING) {
+                const float th = cw[h].z;
+                const float4 a = reinterpret_cast<const float4 *>(pts)[i];
+                return make_float2(fmaf(th, a.z, a.x), fmaf(th, a.w, a.y));
+            } else {
+                return pts[i];
+            }
+        };
+        int e = e0, jb = 0, jend = 0;
+        for (;;) {
+            if (jb >= jend && e < e1) {   // next kept (step, sub-chunk) entry
+                while (m == 0ull && EXACT_DCHECK(hh + 1 < nh, err)) {
                     ++hh;
-                    if (!EXACT_DCHECK(hh < nh, err)) return false;
                     m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
                 }
-                cs = __ffsll((long long)m) - 1;
-                m &= m - 1ull;
-                ++e;
-                ch = hh;
-                i = 0;
+                if (m == 0ull) {   // debug build: the list ended early
+                    e = e1;
+                } else {
+                    const int s = __ffsll((long long)m) - 1;
+                    m &= m - 1ull;
+                    ++e;
+                    jb = s * 32 * ppl;
+                    jend = min(npairs, (s + 1) * 32 * ppl);
+                }
             }
-            uh = ch;
-            uj = (cs * ppl + i) * 32 + lane;
-            ++i;
-            return true;
-        };
-        float best = finf();
-        int bh = -1;
-        auto fold = [&](int uh, float k) {
-            if (uh != bh) {   // warp-uniform
-                best = warp_min_f(best);
-                if (lane == 0 && bh >= 0 && best < finf()) atomicMin(keyh + h0 + bh, f2ord(best));
-                best = finf();
-                bh = uh;
+            const bool more = jb < jend;
+            const int j = jb + lane;   // points 2j and 2j + 1 of step slot hh
+            bool k0 = false, k1 = false;
+            if (more && j < jend) {
+                const float4 qp = pose[h0 + hh];
+                auto near_box = [&](float2 o) {
+                    float px, py;
+                    body_frame(o.x, o.y, qp.x, qp.y, qp.z, qp.w, px, py);
+                    const float ax = fabsf(px - fb.x) - fb.z, ay = fabsf(py - fb.y) - fb.w;
+                    const float l = fmaf(1e-5f, fabsf(px) + fabsf(py), lim);
+                    const float mx = fmaxf(ax, 0.f), my = fmaxf(ay, 0.f);
+                    return ax <= l && ay <= l && fmaf(mx, mx, my * my) <= l * l;   // NaN (masked): false
+                };
+                k0 = near_box(point_at(2 * j, h0 + hh));
+                if (2 * j + 1 < n) k1 = near_box(point_at(2 * j + 1, h0 + hh));
             }
-            best = fminf(best, k);
-        };
-        int ha, ja, hb, jb;
-        while (next(ha, ja)) {
-            const bool two = next(hb, jb);
-            if (!two) { hb = ha; jb = ja; }
-            const bool va = ja < npairs, vb = two && jb < npairs;
-            float px[4], py[4], k[4];
-            pair_at(va ? ja : npairs - 1, h0 + ha, px[0], py[0], px[1], py[1]);
-            pair_at(vb ? jb : npairs - 1, h0 + hb, px[2], py[2], px[3], py[3]);
-            ev.eval4(px, py, k);
-            fold(ha, va ? fminf(k[0], k[1]) : finf());
-            if (two) fold(hb, vb ? fminf(k[2], k[3]) : finf());
+            jb += 32;
+            const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
+            if (b0 | b1) {
+                const unsigned below = (1u << lane) - 1u;
+                const int pos = qn + __popc(b0 & below) + __popc(b1 & below);
+                if (k0) q[pos] = (hh << 12) | (2 * j);
+                if (k1) q[pos + (k0 ? 1 : 0)] = (hh << 12) | (2 * j + 1);
+                qn += __popc(b0) + __popc(b1);
+            }
+            if (qn >= flush_at || (!more && qn > 0)) {
+                // evaluate entries [0, f), f <= 64, and move the rest to the front
+                const int f = min(qn, 64);
+                __syncwarp();
+                const int a = 2 * lane;
+                if (a < f) {
+                    const bool two = a + 1 < f;
+                    int ea = q[a], eb = two ? q[a + 1] : ea;
+                    if (!EXACT_DCHECK((ea & 4095) < n && (ea >> 12) < nh, err)) ea = 0;   // debug build: skip
+                    if (!EXACT_DCHECK((eb & 4095) < n && (eb >> 12) < nh, err)) eb = 0;
+                    const int ha = h0 + (ea >> 12), hb = h0 + (eb >> 12);
+                    const float2 oa = point_at(ea & 4095, ha), ob = point_at(eb & 4095, hb);
+                    const float4 pa = pose[ha], pb = pose[hb];
+                    float pxa, pya, pxb, pyb;
+                    body_frame(oa.x, oa.y, pa.x, pa.y, pa.z, pa.w, pxa, pya);
+                    body_frame(ob.x, ob.y, pb.x, pb.y, pb.z, pb.w, pxb, pyb);
+                    float ka, kb;
+                    ev.eval2(pxa, pya, pxb, pyb, ka, kb);
+                    atomicMin(keyh + ha, f2ord(ka));
+                    if (two) atomicMin(keyh + hb, f2ord(kb));
+                }
+                __syncwarp();
+                for (int i = lane; i < qn - f; i += 32) q[i] = q[f + i];
+                __syncwarp();
+                qn -= f;
+            }
+            if (!more && qn == 0) return;
         }
-        fold(-1, finf());
-        return;
     }
     float best = finf();
     for (int e = e0; e < e1; ++e) {
@@ -930,14 +987,10 @@ __device__ __forceinline__ double phi_obs_d(const MppiP &P, float d) {
 }
 
 struct SampleSmem {
-    union {
-        struct {
-            float4 circ[kStage / kSub];            // sub-chunk bounding circles
-            unsigned msk[2 * EXACT_MAX_HORIZON];   // kept (step, sub-chunk) pairs, 64 bits per step
-            int pre[EXACT_MAX_HORIZON + 1];        // exclusive prefix of their counts
-        };
-        int queue[kQueueAll];   // per-warp queues of kept (step, point) pairs (clouds below kPruneMin)
-    };
+    float4 circ[kStage / kSub];            // sub-chunk bounding circles
+    unsigned msk[2 * EXACT_MAX_HORIZON];   // kept (step, sub-chunk) pairs, 64 bits per step
+    int pre[EXACT_MAX_HORIZON + 1];        // exclusive prefix of their counts
+    int queue[kQueueAll];                  // per-warp queues of kept (step, point) entries
     float4 cw[EXACT_MAX_HORIZON];      // footprint circle centre (world) and t_h per step
     float4 pose[EXACT_MAX_HORIZON];
     float stage[EXACT_MAX_HORIZON];
@@ -1040,7 +1093,7 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     // clouds, one pass) are skipped
     const float cap = V.dmin ? -1.f : fmaxf(P.d_safe, 0.f);
     steps_min_keys<MOVING>(ev, s_pts, n0, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
-                           sm.pre, !V.dmin && N < kPruneMin ? sm.queue : nullptr, V.err);
+                           sm.pre, sm.queue, !V.dmin && N < kPruneMin, V.err);
     for (int base = kS; base < N; base += kS) {   // clouds larger than the stage
         const int n = min(kS, N - base);
         __syncthreads();
@@ -1055,7 +1108,7 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
             __syncthreads();
         }
         steps_min_keys<MOVING>(ev, s_pts, n, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
-                               sm.pre, nullptr, V.err);
+                               sm.pre, sm.queue, false, V.err);
     }
     grid_dep_release();
     __syncthreads();

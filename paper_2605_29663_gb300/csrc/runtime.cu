@@ -148,8 +148,10 @@ extern "C" int exact_footprint_create(int kind, const float *host_data, int n, e
         }
     }
     // bounding circle of the footprint (centre of the bounding box, largest
-    // vertex / box-corner distance), rounded outwards, for the bound that
-    // lets the MPPI kernels skip far point chunks
+    // vertex / box-corner distance) and the bounding box itself (half
+    // extents about that centre), both rounded outwards so that the float
+    // circle and box contain the footprint, for the bounds that let the
+    // MPPI kernels skip far point chunks and far points
     double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
     auto corners = [&](auto &&visit) {
         if (kind == EXACT_FP_POLYGON) {
@@ -172,6 +174,9 @@ extern "C" int exact_footprint_create(int kind, const float *host_data, int n, e
     fp->bcx = (float)bcx;
     fp->bcy = (float)bcy;
     fp->brad = (float)(sqrt(r2) * (1.0 + 1e-6) + 1e-6 + fabs((double)fp->bcx - bcx) + fabs((double)fp->bcy - bcy));
+    const double shift = fabs((double)fp->bcx - bcx) + fabs((double)fp->bcy - bcy);
+    fp->bhx = (float)(0.5 * (hi[0] - lo[0]) * (1.0 + 1e-6) + 1e-6 + shift);
+    fp->bhy = (float)(0.5 * (hi[1] - lo[1]) * (1.0 + 1e-6) + 1e-6 + shift);
     *out = fp;
     return EXACT_OK;
 }
