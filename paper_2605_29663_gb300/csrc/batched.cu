@@ -104,6 +104,11 @@ using namespace exact;
 
 static int batch_grid(exact_batch *b) {
     int per_sm = 0;
+    // the staged points and footprint slots (dynamic) plus the sample state
+    // (static) exceed the default 48 KB per block
+    if (cudaFuncSetAttribute(batched_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) !=
+        cudaSuccess)
+        return EXACT_ECUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_sample_kernel, b->threads, b->smem) !=
         cudaSuccess)
         return EXACT_ECUDA;
@@ -131,8 +136,7 @@ extern "C" int exact_batch_create(int n_scenes, const exact_scene *scenes, exact
         scratch_total += align_up(scene_scratch_bytes(S.params.K, S.params.T, 1), 256);
         // scenes that prune (no d_min output, large cloud) get a spatially ordered cloud copy
         if (!S.dmin && S.n_points >= kPruneMin)
-            scratch_total += align_up((size_t)S.n_points * sizeof(float2), 256) +
-                             align_up((size_t)((S.n_points + kSub - 1) / kSub) * sizeof(float4), 256);
+            scratch_total += align_up((size_t)S.n_points * sizeof(float2), 256) + circle_bytes(S.n_points);
         max_stage = std::max(max_stage, std::min(S.n_points, kStage));
     }
     std::vector<int> sort_list;

@@ -49,7 +49,9 @@ int launch_uniform_sample_t(exact_batch *b, const SceneDev *table, cudaStream_t 
     auto k = batched_sample_kernel_c<FPC>;
     if (b->grid_c <= 0) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, b->threads, b->smem) != cudaSuccess ||
+        // staged points (dynamic) and sample state (static) exceed the default 48 KB per block
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, b->threads, b->smem) != cudaSuccess ||
             per_sm < 1)
             return EXACT_ECUDA;
         b->grid_c = b->sms * per_sm;

@@ -310,6 +310,16 @@ constexpr int kSub = 64;
 constexpr float kPruneSlack = 1e-3f;   // m: far above the float rounding of the distances
 constexpr int kPruneMin = 1024;        // points: smaller clouds are pruned point by point (see steps_min_keys)
 constexpr int kQueueAll = 1024;        // entries of the block's queues of kept (step, point) pairs
+constexpr int kFine = 16;              // points of a fine sub-chunk (a quarter of a sub-chunk)
+constexpr int kQueueFine = 640;        // entries of the block's queues of kept fine sub-chunks
+
+// An ordered cloud of N points carries the circles of its ceil(N / kSub)
+// sub-chunks and, after them (256-byte aligned), those of its ceil(N / kFine)
+// fine sub-chunks.
+__host__ __device__ constexpr int fine_circle_offset(int N) { return (((N + kSub - 1) / kSub) + 15) & ~15; }
+__host__ __device__ constexpr size_t circle_bytes(int N) {
+    return ((size_t)fine_circle_offset(N) + ((((size_t)N + kFine - 1) / kFine + 15) & ~(size_t)15)) * 16u;
+}
 
 template <bool MOVING>
 __device__ __forceinline__ void chunk_circles(const float2 *pts, int n, float4 *circ, int ppl) {
@@ -483,7 +493,9 @@ __device__ __forceinline__ void sort_cloud_block(const float2 *__restrict__ pts,
 
 // Bounding circles (centre, radius, max speed) of the 64-point sub-chunks of
 // an ordered cloud in global memory, one warp per sub-chunk; the same values
-// chunk_circles computes for one staged pass, computed once per cycle.
+// chunk_circles computes for one staged pass, computed once per cycle.  The
+// circles of the 16-point fine sub-chunks (same construction over a half
+// warp's points) follow at circ + fine_circle_offset(N).
 template <bool MOVING>
 __device__ __forceinline__ void cloud_circles(const float2 *__restrict__ pts, const float2 *__restrict__ vel, int N,
                                               float4 *__restrict__ circ) {
@@ -513,10 +525,55 @@ __device__ __forceinline__ void cloud_circles(const float2 *__restrict__ pts, co
         if (lane == 0)
             circ[s] = any ? make_float4(cx, cy, sqrtf(r2) * 1.000001f, MOVING ? sqrtf(v2) * 1.000001f : 0.f)
                           : make_float4(0.f, 0.f, -1.f, 0.f);
+        // fine sub-chunk 2k + (lane >> 4): points k * 32 + lane of this sub-chunk
+        float4 *fine = circ + fine_circle_offset(N);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            float flx = x[k], fly = y[k], fhx = x[k], fhy = y[k], fv2 = 0.f;
+            if (MOVING && x[k] == x[k]) {
+                const int i = s * kSub + k * 32 + lane;
+                fv2 = fmaf(vel[i].x, vel[i].x, vel[i].y * vel[i].y);
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {   // within each half warp; NaN (masked, absent) ignored
+                flx = fminf(flx, __shfl_xor_sync(0xffffffffu, flx, o));
+                fly = fminf(fly, __shfl_xor_sync(0xffffffffu, fly, o));
+                fhx = fmaxf(fhx, __shfl_xor_sync(0xffffffffu, fhx, o));
+                fhy = fmaxf(fhy, __shfl_xor_sync(0xffffffffu, fhy, o));
+                if (MOVING) fv2 = fmaxf(fv2, __shfl_xor_sync(0xffffffffu, fv2, o));
+            }
+            const bool fany = flx <= fhx;
+            const float fcx = 0.5f * (flx + fhx), fcy = 0.5f * (fly + fhy);
+            float fr2 = x[k] == x[k] ? fmaf(x[k] - fcx, x[k] - fcx, (y[k] - fcy) * (y[k] - fcy)) : 0.f;
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) fr2 = fmaxf(fr2, __shfl_xor_sync(0xffffffffu, fr2, o));
+            const int f = s * (kSub / kFine) + 2 * k + (lane >> 4);
+            if ((lane & 15) == 0 && f * kFine < N)
+                fine[f] = fany ? make_float4(fcx, fcy, sqrtf(fr2) * 1.000001f, MOVING ? sqrtf(fv2) * 1.000001f : 0.f)
+                               : make_float4(0.f, 0.f, -1.f, 0.f);
+        }
     }
 }
 
 // ---------------------------------------------------------------- sample phase
+// Position of the k-th (from 0) set bit of m; k < popc(m).
+__device__ __forceinline__ int nth_set_bit64(unsigned long long m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 32; w > 0; w >>= 1) {
+        const unsigned long long low = m & ((1ull << w) - 1ull);
+        const int c = __popcll(low);
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = low;
+        }
+    }
+    return pos;
+}
+
 // Per-step minimum of the body-frame key over n staged points for the steps
 // [h0, h0 + nh) whose poses are in shared memory.  Masked points were staged
 // as NaN, which every evaluator turns into a +inf key (NaN terms are dropped
@@ -536,9 +593,12 @@ __device__ __forceinline__ void cloud_circles(const float2 *__restrict__ pts, co
 //     sub-chunk) list; polygons and shared-memory footprints keep the points
 //     that lie within cap of the footprint's bounding box in that step's
 //     body frame and evaluate them through the warp's queue (queue:
-//     kQueueAll ints of shared memory), rectangle covers evaluate every point
-//     and fold each step's minimum into keyh[h] (one warp shuffle-min and
-//     one shared atomicMin per step run).
+//     kQueueAll ints of shared memory); rectangle covers keep the 16-point
+//     fine sub-chunks whose circles (circf, from the ordered cloud) come
+//     within cap of that box and evaluate them through the queue qfine
+//     (kQueueFine ints), or, without fine circles, evaluate every point and
+//     fold each step's minimum into keyh[h] (one warp shuffle-min and one
+//     shared atomicMin per step run).
 // With queue_points (clouds below kPruneMin) the phases are replaced by a
 // point-level test against the footprint's bounding circle, feeding the
 // same kind of queue.  Pruning never changes a result: cap = d_safe is passed only
@@ -551,7 +611,8 @@ template <bool MOVING = false, class EV>
 __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose,
                                                const float4 *cw, int h0, int nh, unsigned *keyh, int ppl,
                                                const float4 *circ, float cap, unsigned *msk, int *pre,
-                                               int *queue, bool queue_points, int *err = nullptr) {
+                                               int *queue, bool queue_points, const float4 *circf, int *qfine,
+                                               int *err = nullptr) {
     const int npairs = (n + 1) >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nsub = (n + kSub * ppl - 1) / (kSub * ppl);
@@ -861,6 +922,101 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
             if (!more && qn == 0) return;
         }
     }
+    if (circf) {
+        // Rectangle covers with the fine circles of an ordered cloud: the
+        // four 16-point fine sub-chunks of every kept (step, sub-chunk) entry
+        // are tested against the footprint's bounding box in the step's body
+        // frame (one lane per fine sub-chunk, eight entries per warp
+        // iteration, each lane decoding its own entry from pre and msk); the
+        // kept ones go through the warp's queue and are evaluated four at a
+        // time, eight lanes (one pair each) per fine sub-chunk, whose step
+        // minimum is folded over the eight lanes and into keyh[h] with one
+        // shared atomicMin.  Every point of a fine sub-chunk lies within its
+        // circle (radius grown by t_h times its largest speed when MOVING),
+        // sd_F >= sd_box for a footprint F inside the box, and sd_box is
+        // 1-Lipschitz, so a dropped fine sub-chunk holds no point within cap.
+        const float4 fb = ev.box();
+        const int capf = kQueueFine / nwarps;   // >= 40 for up to 16 warps: 3 left + 32 added fit
+        int *q = qfine + warp * capf;
+        int qn = 0;   // warp-uniform
+        const int nfine = (n + kFine - 1) / kFine;
+        for (int e = e0;; e += 8) {
+            const bool more = e < e1;
+            const int my = e + (lane >> 2);
+            bool keep = false;
+            int code = 0;
+            if (more && my < e1) {
+                int lo = 0, hi = nh - 1;   // the step holding entry my: the last with pre <= my
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (pre[mid] <= my) lo = mid; else hi = mid - 1;
+                }
+                const unsigned long long mm = ((unsigned long long)msk[2 * lo + 1] << 32) | msk[2 * lo];
+                const int fi = nth_set_bit64(mm, my - pre[lo]) * (kSub / kFine) + (lane & 3);
+                if (fi < nfine) {
+                    const float4 c = circf[fi];
+                    if (c.z >= 0.f) {
+                        const float4 qp = pose[h0 + lo];
+                        float px, py;
+                        body_frame(c.x, c.y, qp.x, qp.y, qp.z, qp.w, px, py);
+                        float reach = c.z + 1e-5f * (fabsf(c.x) + fabsf(c.y) + fabsf(qp.x) + fabsf(qp.y));
+                        if (MOVING) reach = fmaf(cw[h0 + lo].z, c.w, reach);
+                        const float l = reach + lim;
+                        const float ax = fabsf(px - fb.x) - fb.z, ay = fabsf(py - fb.y) - fb.w;
+                        const float mx = fmaxf(ax, 0.f), my2 = fmaxf(ay, 0.f);
+                        keep = ax <= l && ay <= l && fmaf(mx, mx, my2 * my2) <= l * l;
+                    }
+                }
+                code = (lo << 12) | fi;
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, keep);
+            if (keep) q[qn + __popc(b & ((1u << lane) - 1u))] = code;
+            qn += __popc(b);
+            while (qn >= 4 || (!more && qn > 0)) {
+                // evaluate entries [0, f), f <= 4, and move the rest to the front
+                const int f = min(qn, 4);
+                __syncwarp();
+                const int slot = lane >> 3, pr = lane & 7;
+                float best = finf();
+                int sh = 0;
+                if (slot < f) {
+                    int ce = q[slot];
+                    if (!EXACT_DCHECK((ce >> 12) < nh && (ce & 4095) < nfine, err)) ce = 0;   // debug build: skip
+                    sh = ce >> 12;
+                    const int j = (ce & 4095) * (kFine / 2) + pr;   // pair j of the staged points
+                    if (j < npairs) {
+                        const int h = h0 + sh;
+                        const float4 qp = pose[h];
+                        float2 o0, o1;
+                        if constexpr (MOVING) {
+                            const float th = cw[h].z;
+                            const float4 *p4 = reinterpret_cast<const float4 *>(pts);
+                            const float4 a0 = p4[2 * j], a1 = p4[min(2 * j + 1, n - 1)];
+                            o0 = make_float2(fmaf(th, a0.z, a0.x), fmaf(th, a0.w, a0.y));
+                            o1 = make_float2(fmaf(th, a1.z, a1.x), fmaf(th, a1.w, a1.y));
+                        } else {
+                            o0 = pts[2 * j];
+                            o1 = pts[min(2 * j + 1, n - 1)];
+                        }
+                        float px0, py0, px1, py1;
+                        body_frame(o0.x, o0.y, qp.x, qp.y, qp.z, qp.w, px0, py0);
+                        body_frame(o1.x, o1.y, qp.x, qp.y, qp.z, qp.w, px1, py1);
+                        float k0, k1;
+                        ev.eval2(px0, py0, px1, py1, k0, k1);
+                        best = fminf(k0, k1);
+                    }
+                }
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+                if (slot < f && pr == 0 && best < finf()) atomicMin(keyh + h0 + sh, f2ord(best));
+                __syncwarp();
+                for (int i = lane; i < qn - f; i += 32) q[i] = q[f + i];
+                __syncwarp();
+                qn -= f;
+            }
+            if (!more) return;
+        }
+    }
     float best = finf();
     for (int e = e0; e < e1; ++e) {
         if (!EXACT_DCHECK(hh < nh, err)) break;
@@ -990,7 +1146,11 @@ struct SampleSmem {
     float4 circ[kStage / kSub];            // sub-chunk bounding circles
     unsigned msk[2 * EXACT_MAX_HORIZON];   // kept (step, sub-chunk) pairs, 64 bits per step
     int pre[EXACT_MAX_HORIZON + 1];        // exclusive prefix of their counts
-    int queue[kQueueAll];                  // per-warp queues of kept (step, point) entries
+    union {
+        int queue[kQueueAll];              // per-warp queues of kept (step, point) entries
+        float4 circf[kStage / kFine];      // fine sub-chunk circles (rectangle covers)
+    };
+    int qfine[kQueueFine];                 // per-warp queues of kept (step, fine sub-chunk) entries
     float4 cw[EXACT_MAX_HORIZON];      // footprint circle centre (world) and t_h per step
     float4 pose[EXACT_MAX_HORIZON];
     float stage[EXACT_MAX_HORIZON];
@@ -1081,11 +1241,17 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     // sub-chunk circles: copied from the ordered cloud's (64-point sub-chunks),
     // or computed from the staged points
     const bool pre_circ = circ != nullptr && pairs_per_lane == 1;
+    // rectangle covers test the fine sub-chunks of the kept sub-chunks too
+    // (polygons test single points instead; see steps_min_keys)
+    const bool fine = pre_circ && !EV::kBoxTest;
+    const float4 *circ_f = fine ? circ + fine_circle_offset(N) : nullptr;
     if (!staged && prune) {
         if (pre_circ)
             for (int s = threadIdx.x; s < (n0 + kSub - 1) / kSub; s += blockDim.x) sm.circ[s] = circ[s];
         else
             chunk_circles<MOVING>(s_pts, n0, sm.circ, pairs_per_lane);
+        if (fine)
+            for (int s = threadIdx.x; s < (n0 + kFine - 1) / kFine; s += blockDim.x) sm.circf[s] = circ_f[s];
         __syncthreads();
     }
     // without a d_min output the costs only need min(d_min, d_safe): far
@@ -1093,7 +1259,7 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     // clouds, one pass) are skipped
     const float cap = V.dmin ? -1.f : fmaxf(P.d_safe, 0.f);
     steps_min_keys<MOVING>(ev, s_pts, n0, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
-                           sm.pre, sm.queue, !V.dmin && N < kPruneMin, V.err);
+                           sm.pre, sm.queue, !V.dmin && N < kPruneMin, fine ? sm.circf : nullptr, sm.qfine, V.err);
     for (int base = kS; base < N; base += kS) {   // clouds larger than the stage
         const int n = min(kS, N - base);
         __syncthreads();
@@ -1105,10 +1271,13 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
                 for (int s = threadIdx.x; s < (n + kSub - 1) / kSub; s += blockDim.x) sm.circ[s] = circ[base / kSub + s];
             else
                 chunk_circles<MOVING>(s_pts, n, sm.circ, pairs_per_lane);
+            if (fine)
+                for (int s = threadIdx.x; s < (n + kFine - 1) / kFine; s += blockDim.x)
+                    sm.circf[s] = circ_f[base / kFine + s];
             __syncthreads();
         }
         steps_min_keys<MOVING>(ev, s_pts, n, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
-                               sm.pre, sm.queue, false, V.err);
+                               sm.pre, sm.queue, false, fine ? sm.circf : nullptr, sm.qfine, V.err);
     }
     grid_dep_release();
     __syncthreads();

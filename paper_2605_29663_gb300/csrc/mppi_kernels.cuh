@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(kBlock) mppi_validate_kernel(const SceneView V
 }
 
 // One block rewrites the cloud in spatial order (see sort_cloud_block) and
-// takes the bounding circles of its 64-point sub-chunks.
+// takes the bounding circles of its 64-point sub-chunks and of its 16-point
+// fine sub-chunks.
 template <bool MOVING>
 __global__ void __launch_bounds__(kSortThreads)
 cloud_sort_kernel(const float2 *pts, const float2 *vel, const uint8_t *mask, int N, float2 *opts, float2 *ovel,
@@ -62,10 +63,10 @@ cloud_sort_kernel(const float2 *pts, const float2 *vel, const uint8_t *mask, int
 }
 
 // Bytes of the spatially ordered cloud copy (points, velocities when
-// predicted, sub-chunk circles) that follows a scene's scratch in the arena.
+// predicted, sub-chunk and fine sub-chunk circles) that follows a scene's
+// scratch in the arena.
 inline size_t cloud_copy_bytes(int N, bool moving) {
-    return align_up((size_t)N * sizeof(float2), 256) * (moving ? 2 : 1) +
-           align_up((size_t)((N + kSub - 1) / kSub) * sizeof(float4), 256);
+    return align_up((size_t)N * sizeof(float2), 256) * (moving ? 2 : 1) + circle_bytes(N);
 }
 
 
