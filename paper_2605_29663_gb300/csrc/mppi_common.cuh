@@ -97,13 +97,19 @@ __device__ __forceinline__ void warp_rollout(const MppiP &P, float x0, float y0,
     const int base = lane * per;
     float rate[kMaxPerLane];
     float tot = 0.f;
+    // elements e >= per (warp-uniform) hold no step: their work is skipped
 #pragma unroll
     for (int e = 0; e < kMaxPerLane; ++e) {
         const int h = base + e;
         const bool ok = e < per && h < T;
+        rate[e] = 0.f;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) R.u[e][j] = (ok && j < P.nu) ? ufetch(h, j) : 0.f;
-        rate[e] = ok ? heading_rate(P.model, P.wheelbase, R.u[e][0], R.u[e][1], R.u[e][2]) * P.dt : 0.f;
+        for (int j = 0; j < 3; ++j) R.u[e][j] = 0.f;
+        if (e < per) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) R.u[e][j] = (ok && j < P.nu) ? ufetch(h, j) : 0.f;
+            rate[e] = ok ? heading_rate(P.model, P.wheelbase, R.u[e][0], R.u[e][1], R.u[e][2]) * P.dt : 0.f;
+        }
         tot += rate[e];
     }
     // theta_h (before step h): exclusive prefix over all steps
@@ -115,12 +121,15 @@ __device__ __forceinline__ void warp_rollout(const MppiP &P, float x0, float y0,
     for (int e = 0; e < kMaxPerLane; ++e) {
         thb[e] = th0 + run;
         run += rate[e];
-        float sn, cs;
-        sincosf(thb[e], &sn, &cs);
-        planar_velocity(P.model, cs, sn, R.u[e][0], R.u[e][1], fx[e], fy[e]);
-        const bool ok = e < per && base + e < T;
-        fx[e] = ok ? fx[e] * P.dt : 0.f;
-        fy[e] = ok ? fy[e] * P.dt : 0.f;
+        fx[e] = fy[e] = 0.f;
+        if (e < per) {
+            float sn, cs;
+            sincosf(thb[e], &sn, &cs);
+            planar_velocity(P.model, cs, sn, R.u[e][0], R.u[e][1], fx[e], fy[e]);
+            const bool ok = base + e < T;
+            fx[e] = ok ? fx[e] * P.dt : 0.f;
+            fy[e] = ok ? fy[e] * P.dt : 0.f;
+        }
         tx += fx[e];
         ty += fy[e];
     }

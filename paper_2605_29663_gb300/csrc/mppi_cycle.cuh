@@ -683,25 +683,27 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
         return;
     }
     if constexpr (EV::kQueueOk) if (queue_points) {
-        // Point-level pruning (clouds below kPruneMin, no sort, no circles):
-        // the warp walks its contiguous share of the (step, pair) units; each
-        // lane keeps a point only if it lies within the footprint's bounding
-        // circle at that step plus cap (and the slack of the chunk test, taken
-        // for a circle of radius 0); kept (step, point) entries are appended to
-        // the warp's queue and evaluated 64 at a time, two per lane (the two
-        // lanes of the packed evaluator may hold points of different steps:
-        // the footprint is the same in every body frame), each key folded into
-        // its step's minimum with a shared atomicMin.  A warp's queue holds
-        // kQueueAll / warps entries: with 128 or more a flush waits for 64
-        // entries, with fewer every iteration that adds some flushes them.
+        // Point-level pruning (clouds below kPruneMin, no sort, no circles).
+        // Every warp first bounds the sample's trajectory by one circle
+        // (cb, rb) that holds the footprint's bounding circle at every step
+        // plus cap and the slack of the chunk test (taken for a circle of
+        // radius 0), then walks its contiguous share of the point pairs: a
+        // point outside that circle (grown by t_max |v|_1 for predicted
+        // points) is farther than cap from the footprint at every step; each
+        // point inside is tested against every step's circle, one lane per
+        // step.  Kept (step, point) entries are appended to the warp's queue
+        // and evaluated 64 at a time, two per lane (the two lanes of the
+        // packed evaluator may hold points of different steps: the footprint
+        // is the same in every body frame), each key folded into its step's
+        // minimum with a shared atomicMin.  A warp's queue holds kQueueAll /
+        // warps entries: with 128 or more a flush waits for 64 entries, with
+        // fewer every iteration that adds some flushes them.
         const float3 bc = ev.bound();
         const float lim = cap + kPruneSlack;
         const int cap_q = kQueueAll / nwarps;
         const int flush_at = cap_q >= 128 ? 64 : 1;
         int *q = queue + warp * cap_q;
         int qn = 0;   // warp-uniform
-        const long long units = (long long)nh * npairs;
-        const int e0 = (int)((units * warp) / nwarps), e1 = (int)((units * (warp + 1)) / nwarps);
         auto point_at = [&](int i, int h) -> float2 {
             if constexpr (MOVING) {
                 const float th = cw[h].z;
@@ -732,46 +734,79 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
             }
             __syncwarp();
         };
-        // lane's first unit, then advance by 32 units per iteration
-        int hh = 0, j = 0;
-        if (e0 + lane < e1) {
-            hh = (e0 + lane) / npairs;
-            j = e0 + lane - hh * npairs;
+        // the trajectory's circle: centre of the step circles' bounding box,
+        // radius max_h |cw_h - cb| + reach_h with a relative margin far above
+        // the rounding of the step tests
+        float lx = finf(), ly = finf(), hx = -finf(), hy = -finf(), tmax = 0.f;
+        for (int k = lane; k < nh; k += 32) {
+            const float4 c = cw[h0 + k];
+            lx = fminf(lx, c.x); hx = fmaxf(hx, c.x); ly = fminf(ly, c.y); hy = fmaxf(hy, c.y);
+            tmax = fmaxf(tmax, c.z);
         }
-        for (int base = e0; base < e1; base += 32) {
-            bool k0 = false, k1 = false;
-            const int i0 = 2 * j, i1 = 2 * j + 1;
-            if (base + lane < e1) {
-                const float4 c = cw[h0 + hh];
-                const float reach = bc.z + lim + 1e-5f * (fabsf(c.x) + fabsf(c.y));
-                const float2 o0 = point_at(i0, h0 + hh);
-                const float dx0 = o0.x - c.x, dy0 = o0.y - c.y;
-                const float f0 = fmaf(1e-5f, fabsf(o0.x) + fabsf(o0.y), reach);
-                k0 = fmaf(dx0, dx0, dy0 * dy0) <= f0 * f0;   // NaN (masked) never kept
-                if (i1 < n) {
-                    const float2 o1 = point_at(i1, h0 + hh);
-                    const float dx1 = o1.x - c.x, dy1 = o1.y - c.y;
-                    const float f1 = fmaf(1e-5f, fabsf(o1.x) + fabsf(o1.y), reach);
-                    k1 = fmaf(dx1, dx1, dy1 * dy1) <= f1 * f1;
+        lx = warp_min_f(lx); ly = warp_min_f(ly); hx = -warp_min_f(-hx); hy = -warp_min_f(-hy);
+        if (MOVING) tmax = -warp_min_f(-tmax);
+        const float cbx = 0.5f * (lx + hx), cby = 0.5f * (ly + hy);
+        float rb = 0.f;
+        for (int k = lane; k < nh; k += 32) {
+            const float4 c = cw[h0 + k];
+            const float dx = c.x - cbx, dy = c.y - cby;
+            rb = fmaxf(rb, sqrtf(fmaf(dx, dx, dy * dy)) + bc.z + lim + 1e-5f * (fabsf(c.x) + fabsf(c.y)));
+        }
+        rb = -warp_min_f(-rb);
+        rb = fmaf(rb, 1e-5f, rb) + 1e-5f;
+        auto near_path = [&](int i) {   // NaN (masked) never kept
+            float x, y, g = rb;
+            if constexpr (MOVING) {
+                const float4 a = reinterpret_cast<const float4 *>(pts)[i];
+                x = a.x; y = a.y;
+                g = fmaf(tmax * 1.0001f, fabsf(a.z) + fabsf(a.w), g);
+            } else {
+                x = pts[i].x; y = pts[i].y;
+            }
+            g = fmaf(1e-5f, fabsf(x) + fabsf(y), g);
+            const float dx = x - cbx, dy = y - cby;
+            return fmaf(dx, dx, dy * dy) <= g * g;
+        };
+        const int p0 = (int)(((long long)npairs * warp) / nwarps), p1 = (int)(((long long)npairs * (warp + 1)) / nwarps);
+        for (int pb = p0; pb < p1; pb += 32) {
+            const int j = pb + lane;
+            const bool c0 = j < p1 && near_path(2 * j);
+            const bool c1 = j < p1 && 2 * j + 1 < n && near_path(2 * j + 1);
+            unsigned b0 = __ballot_sync(0xffffffffu, c0), b1 = __ballot_sync(0xffffffffu, c1);
+            while (b0 | b1) {   // the candidates in lane order, each against every step
+                int i;
+                if (b0) {
+                    i = 2 * (pb + __ffs(b0) - 1);
+                    b0 &= b0 - 1u;
+                } else {
+                    i = 2 * (pb + __ffs(b1) - 1) + 1;
+                    b1 &= b1 - 1u;
+                }
+                for (int k0 = 0; k0 < nh; k0 += 32) {
+                    const int k = k0 + lane;
+                    bool keep = false;
+                    if (k < nh) {
+                        const float4 c = cw[h0 + k];
+                        const float reach = bc.z + lim + 1e-5f * (fabsf(c.x) + fabsf(c.y));
+                        const float2 o = point_at(i, h0 + k);
+                        const float dx = o.x - c.x, dy = o.y - c.y;
+                        const float f = fmaf(1e-5f, fabsf(o.x) + fabsf(o.y), reach);
+                        keep = fmaf(dx, dx, dy * dy) <= f * f;
+                    }
+                    const unsigned bk = __ballot_sync(0xffffffffu, keep);
+                    if (bk) {
+                        if (keep) q[qn + __popc(bk & ((1u << lane) - 1u))] = (k << 12) | i;
+                        qn += __popc(bk);
+                        if (qn >= flush_at) {
+                            const int f = min(qn, 64);
+                            flush(f);
+                            for (int e = lane; e < qn - f; e += 32) q[e] = q[f + e];
+                            __syncwarp();
+                            qn -= f;
+                        }
+                    }
                 }
             }
-            const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
-            if (b0 | b1) {
-                const unsigned below = (1u << lane) - 1u;
-                const int pos = qn + __popc(b0 & below) + __popc(b1 & below);
-                if (k0) q[pos] = (hh << 12) | i0;
-                if (k1) q[pos + (k0 ? 1 : 0)] = (hh << 12) | i1;
-                qn += __popc(b0) + __popc(b1);
-                if (qn >= flush_at) {
-                    const int f = min(qn, 64);
-                    flush(f);
-                    for (int e = lane; e < qn - f; e += 32) q[e] = q[f + e];
-                    __syncwarp();
-                    qn -= f;
-                }
-            }
-            j += 32;
-            while (j >= npairs) { j -= npairs; ++hh; }
         }
         if (qn > 0) flush(qn);
         return;
