@@ -52,8 +52,10 @@ constexpr size_t kArenaHeader = 256;
 struct ArenaHeader {
     unsigned long long beta_enc;   // ~order(J~) of the best sample, via atomicMax; 0 = empty
     unsigned ticket[2];            // finished update / validation blocks
-    int bad;                       // validation failed
+    int bad;                       // validation failed (written by the last validation block)
+    unsigned long long vticket;    // validation blocks finished (low word) and failed (high word)
 };
+static_assert(sizeof(ArenaHeader) <= 64, "the batched step clears 64 bytes of control words per scene");
 
 template <int E>
 inline PolyC<E> make_poly(const exact_footprint *fp) {

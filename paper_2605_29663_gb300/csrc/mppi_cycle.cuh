@@ -1437,7 +1437,7 @@ struct ValidateSmem {
     float4 pose;
     float Z;
     float mn[32];
-    bool last;
+    bool last, ok;
 };
 
 // Block (step h, point chunk c) of a scene's validation (blockDim == kBlock).
@@ -1499,15 +1499,8 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
         sm.U[e] = v;
         if (self == 0 && V.U_upd_out) V.U_upd_out[e] = v;
     }
-    if (V.weights || V.costs) {
-        const int r0 = (int)(((long long)K * self) / nblocks), r1 = (int)(((long long)K * (self + 1)) / nblocks);
-        for (int r = r0 + tid; r < r1; r += kBlock) {
-            if (V.weights) V.weights[r] = __ldcg(V.wt + r) * invZ;
-            if (V.costs) V.costs[r] = (float)V.Jt[r];
-        }
-    }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0) {   // the nominal's rollout on warp 0, the other warps share out the outputs
         LaneRollout R;
         warp_rollout(P, V.state[0], V.state[1], V.state[2], [&](int hh, int j) { return clamp_u(P, j, sm.U[hh * nu + j]); },
                      R);
@@ -1518,6 +1511,12 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
                 sincosf(R.th[q], &sn, &cs);
                 sm.pose = make_float4(R.x[q], R.y[q], cs, sn);
             }
+        }
+    } else if (V.weights || V.costs) {
+        const int r0 = (int)(((long long)K * self) / nblocks), r1 = (int)(((long long)K * (self + 1)) / nblocks);
+        for (int r = r0 + tid - 32; r < r1; r += kBlock - 32) {
+            if (V.weights) V.weights[r] = __ldcg(V.wt + r) * invZ;
+            if (V.costs) V.costs[r] = (float)V.Jt[r];
         }
     }
     __syncthreads();
@@ -1567,15 +1566,20 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
         float b = sm.mn[0];
         for (int w = 1; w < kBlock / 32; ++w) b = fminf(b, sm.mn[w]);
         const float d = b == finf() ? finf() : ev.dist(b);
-        if (!(d >= P.d_safe)) atomicExch(&V.hdr->bad, 1);
+        const bool bad = !(d >= P.d_safe);
         if (V.nom_cost) atomicMax(V.vkey + h, ~f2ord(b));
         __threadfence();
-        sm.last = atomicAdd(&V.hdr->ticket[1], 1u) == (unsigned)nblocks - 1;
+        // one 64-bit ticket: finished blocks in the low word, failed ones in
+        // the high word, so the last block learns the outcome from its own
+        // atomic
+        const unsigned long long t = atomicAdd(&V.hdr->vticket, bad ? 0x100000001ull : 1ull);
+        sm.last = (unsigned)t == (unsigned)nblocks - 1;
+        sm.ok = (t >> 32) == 0ull && !bad;
     }
     __syncthreads();
     if (!sm.last) return;
     __threadfence();
-    const int ok = atomicAdd(&V.hdr->bad, 0) == 0;
+    const int ok = sm.ok ? 1 : 0;
     for (int e = tid; e < TN; e += kBlock) {
         const float v = sm.U[e];
         if (e < nu && V.u_star) V.u_star[e] = ok ? v : 0.f;
@@ -1583,6 +1587,7 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
     }
     if (tid == 0) {
         if (V.valid) *V.valid = ok;
+        V.hdr->bad = ok ? 0 : 1;
         V.hdr->beta_enc = 0ull;
     }
     if (V.nom_cost && warp == 0) {

@@ -24,6 +24,7 @@ mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev, const float4 *cir
         // the validation kernel that follows on the stream counts its
         // finished blocks on this ticket: start it from zero
         V.hdr->ticket[1] = 0u;
+        V.hdr->vticket = 0ull;
         V.hdr->bad = 0;
     }
     // pair: block b takes samples 2b and 2b + 1; else sample b / parts,
