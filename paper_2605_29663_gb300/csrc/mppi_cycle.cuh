@@ -1170,11 +1170,47 @@ __device__ __forceinline__ void stage_points(float2 *dst, const float2 *__restri
     }
 }
 
-// phi_obs (Sec. IV-E) in double: its terms are large (w_coll scale) and are
-// summed over the horizon.
-__device__ __forceinline__ double phi_obs_d(const MppiP &P, float d) {
-    const double gap = fmax((double)P.d_safe - (double)d, 0.0);
-    return (d < 0.f ? (double)P.w_coll : 0.0) + (double)P.w_rep * gap * gap;
+// Float-float numbers hi + lo (|lo| <= ulp(hi) / 2, about 48 significant
+// bits) for the cost sums: the terms are large (w_coll, w_inf scale) and are
+// summed over the horizon, which needs more than float precision; FP64 would
+// give it, but a dependent FP64 operation takes about 65 cycles on this GPU
+// against under 5 for FP32.  two_sum is Knuth's error-free sum; ff_add adds
+// the low parts and renormalises with Dekker's fast two-sum.  Both are
+// commutative bit for bit, so a butterfly reduction leaves the same value on
+// every lane.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return ff{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const ff s = two_sum(a.hi, b.hi);
+    const float e = s.lo + (a.lo + b.lo), h = s.hi + e;
+    return ff{h, e - (h - s.hi)};
+}
+__device__ __forceinline__ ff ff_add(ff a, float b) { return ff_add(a, ff{b, 0.f}); }
+__device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff warp_sum_ff(ff a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        a = ff_add(a, ff{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)});
+    return a;
+}
+
+// acc + phi_obs(d) (Sec. IV-E): w_coll I(d < 0) + w_rep max(d_safe - d, 0)^2,
+// the gap exact as a float-float and its square and product kept to about
+// 48 bits.  A non-finite d adds nothing.
+__device__ __forceinline__ ff add_phi_obs(const MppiP &P, float d, ff acc) {
+    if (d < 0.f) acc = ff_add(acc, P.w_coll);
+    const ff g = two_sum(P.d_safe, -d);
+    if (g.hi > 0.f) {
+        const float p = g.hi * g.hi, pe = fmaf(g.hi, g.hi, -p) + 2.f * g.hi * g.lo;
+        const float q = P.w_rep * p, qe = fmaf(P.w_rep, p, -q) + P.w_rep * pe;
+        acc = ff_add(acc, ff{q, qe});
+    }
+    return acc;
 }
 
 struct SampleSmem {
@@ -1330,23 +1366,25 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     }
     if (warp < ns) {
         const int rs = warp == 0 ? r : r2, off = warp * T, lane = threadIdx.x & 31;
-        double acc = 0.0;
+        ff acc{0.f, 0.f};
         bool unsafe = false;
         for (int h = lane; h < T; h += 32) {
             const float key = ord2f(sm.key[off + h]);
             const float d = key == finf() ? finf() : ev.dist(key);
             if (V.dmin) V.dmin[(size_t)rs * T + h] = d;
-            acc += (double)sm.stage[off + h] + phi_obs_d(P, d);
+            acc = add_phi_obs(P, d, ff_add(acc, sm.stage[off + h]));
             unsafe |= d < P.d_safe;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        acc = warp_sum_ff(acc);
         const bool chi = __any_sync(0xffffffffu, unsafe);
         if (lane == 0) {
-            // J~ = J + w_inf I(chi) in double (Sec. IV-E); beta = min J~ is
-            // gathered with one 64-bit atomic per sample into the scene's
-            // header (complemented key; 0 = empty)
-            const double jt = acc + (double)sm.term[warp] + (chi ? (double)P.w_inf : 0.0);
+            // J~ = J + w_inf I(chi) (Sec. IV-E), summed as a float-float and
+            // kept as a double; beta = min J~ is gathered with one 64-bit
+            // atomic per sample into the scene's header (complemented key;
+            // 0 = empty)
+            acc = ff_add(acc, sm.term[warp]);
+            if (chi) acc = ff_add(acc, P.w_inf);
+            const double jt = ff_to_d(acc);
             V.Jt[rs] = jt;
             atomicMax(&V.hdr->beta_enc, ~d2ord(jt));
         }
@@ -1594,7 +1632,7 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
         LaneRollout R;
         warp_rollout(P, V.state[0], V.state[1], V.state[2], [&](int hh, int j) { return clamp_u(P, j, sm.U[hh * nu + j]); },
                      R);
-        double acc = 0.0;
+        ff acc{0.f, 0.f};
 #pragma unroll
         for (int e = 0; e < kMaxPerLane; ++e) {
             const int hh = lane * R.per + e;
@@ -1603,12 +1641,12 @@ __device__ __forceinline__ void validate_body(const SceneView &V, const EV &ev, 
                 const float stage = fmaf(P.w_goal, guidance_dist(R.x[e], R.y[e], V.wp, V.W), P.w_ctrl * u2);
                 const float key = ord2f(~atomicExch(V.vkey + hh, 0u));
                 const float d = key == finf() ? finf() : ev.dist(key);
-                acc += (double)stage + phi_obs_d(P, d);
+                acc = add_phi_obs(P, d, ff_add(acc, stage));
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) *V.nom_cost = (float)(acc + (double)(P.w_term * guidance_dist(R.qTx, R.qTy, V.wp, V.W)));
+        acc = warp_sum_ff(acc);
+        if (lane == 0)
+            *V.nom_cost = (float)ff_to_d(ff_add(acc, P.w_term * guidance_dist(R.qTx, R.qTy, V.wp, V.W)));
     }
 }
 
