@@ -1410,6 +1410,10 @@ __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSme
     const int r0 = b * V.upd_chunk, r1 = min(K, r0 + V.upd_chunk), nr = r1 - r0;
     const float *U = V.U;
 
+    // the validation launch may place its blocks now: they read the nominal
+    // and then wait for this grid (PDL lets them in only once every block of
+    // this grid has started, so they never take a slot this grid needs)
+    grid_dep_release();
     const float *src = V.noise + (size_t)r0 * TN;
     const int n = nr * TN;
     bool finite = true;
@@ -1463,7 +1467,6 @@ __device__ __forceinline__ void update_body(const SceneView &V, int b, UpdateSme
         for (int w = 0; w < kUpdBlock / 32; ++w) zb += sm.f[w];
         part[TN] = zb;
     }
-    grid_dep_release();
 }
 
 // ---------------------------------------------------------------- validation
