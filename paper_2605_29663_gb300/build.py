@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(LIB_DIR, "libexact_mppi.so")
 LIB_PATH_DEBUG = os.path.join(LIB_DIR, "libexact_mppi_debug.so")
 BUILD_DIR_DEBUG = os.path.join(PKG, "_build_debug")
 
-SOURCES = ["runtime.cu", "sdf_batch.cu", "mppi.cu", "batched.cu", "noalloc.cu", "mlp.cu", "features.cu", "hybrid.cu", "mppi_predicted.cu", "mppi_dense.cu", "batched_uniform_small.cu", "batched_uniform_large.cu"]
+SOURCES = ["runtime.cu", "sdf_batch.cu", "mppi.cu", "batched.cu", "noalloc.cu", "mlp.cu", "features.cu", "hybrid.cu", "mppi_predicted.cu", "mppi_dense.cu", "mppi_points.cu", "batched_uniform_small.cu", "batched_uniform_large.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--ptxas-options=-O3", f"-I{INCLUDE}", f"-I{CSRC}"]

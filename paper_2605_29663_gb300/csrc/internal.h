@@ -126,6 +126,36 @@ int with_footprint(const exact_footprint *fp, F &&f) {
     }
 }
 
+// with_footprint for the footprints whose MPPI evaluator prunes point by
+// point (rectangle covers, polygons of up to 16 edges); EXACT_EINVAL for any
+// other.
+template <class F>
+int with_small_footprint(const exact_footprint *fp, F &&f) {
+    if (fp->kind == EXACT_FP_POLYGON) {
+        switch (fp->n_pad) {
+        case 4: return f(make_poly<4>(fp));
+        case 6: return f(make_poly<6>(fp));
+        case 8: return f(make_poly<8>(fp));
+        case 10: return f(make_poly<10>(fp));
+        case 12: return f(make_poly<12>(fp));
+        case 14: return f(make_poly<14>(fp));
+        case 16: return f(make_poly<16>(fp));
+        default: return EXACT_EINVAL;
+        }
+    }
+    switch (fp->n_pad) {
+    case 1: return f(make_rect<1>(fp));
+    case 2: return f(make_rect<2>(fp));
+    case 3: return f(make_rect<3>(fp));
+    case 4: return f(make_rect<4>(fp));
+    case 5: return f(make_rect<5>(fp));
+    case 6: return f(make_rect<6>(fp));
+    case 7: return f(make_rect<7>(fp));
+    case 8: return f(make_rect<8>(fp));
+    default: return EXACT_EINVAL;
+    }
+}
+
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? EXACT_OK : EXACT_ECUDA; }
 
 }  // namespace exact

@@ -183,10 +183,11 @@ int mppi_step_impl(exact_ctx *ctx, const float *state, const float *cloud, const
 }
 
 // Clouds with point velocities go to mppi_predicted.cu.  Static clouds go to
-// the register-capped kernels of mppi_dense.cu when the footprint is small (a
-// rectangle cover or at most 16 edges: larger polygons need more registers
-// than the cap leaves) and either the sample grid exceeds four blocks per SM
-// or the cloud is pruned point by point; else to the unbounded ones here.
+// the register-capped kernels when the footprint is small (a rectangle cover
+// or at most 16 edges: larger polygons need more registers than the cap
+// leaves): those of mppi_points.cu when the cloud is pruned point by point,
+// those of mppi_dense.cu when the sample grid exceeds four blocks per SM;
+// else to the unbounded ones here.
 int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
                  int sms) {
     if (sms <= 0) sms = 148;
@@ -195,8 +196,8 @@ int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st,
     // small clouds without a d_min output are pruned point by point: little
     // evaluation work is left, and the capped kernel's occupancy wins
     const bool queued = !V.dmin && V.N < kPruneMin;
-    if (small_fp && ((long long)V.P.K * V.parts > 4LL * sms || queued))
-        return launch_cycle_dense(V, fp, st, pdl, circ, sms);
+    if (small_fp && queued) return launch_cycle_points(V, fp, st, pdl, circ, sms);
+    if (small_fp && (long long)V.P.K * V.parts > 4LL * sms) return launch_cycle_dense(V, fp, st, pdl, circ, sms);
     return launch_cycle_t<false, 0>(V, fp, st, pdl, circ, sms);
 }
 

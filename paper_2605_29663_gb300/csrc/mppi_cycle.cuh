@@ -311,6 +311,11 @@ constexpr float kPruneSlack = 1e-3f;   // m: far above the float rounding of the
 constexpr int kPruneMin = 1024;        // points: smaller clouds are pruned point by point (see steps_min_keys)
 constexpr int kQueueAll = 1024;        // entries of the block's queues of kept (step, point) pairs
 constexpr int kFine = 16;              // points of a fine sub-chunk (a quarter of a sub-chunk)
+// Sample-phase code paths compiled into a kernel: every path (chosen per
+// call), or only the point-level pruning of small clouds (the caller passes
+// no d_min output and fewer than kPruneMin points) -- a smaller kernel whose
+// code each block fetches once per cycle.
+constexpr int kPathAny = 0, kPathPoints = 1;
 constexpr int kQueueFine = 640;        // entries of the block's queues of kept fine sub-chunks
 
 // An ordered cloud of N points carries the circles of its ceil(N / kSub)
@@ -607,7 +612,7 @@ __device__ __forceinline__ int nth_set_bit64(unsigned long long m, int k) {
 // than that.  Without pruning (cap < 0) items (step h, chunk of 128 pairs)
 // are dealt to the warps round-robin, each ending in one warp shuffle-min and
 // one shared atomicMin on the key of step h.
-template <bool MOVING = false, class EV>
+template <bool MOVING = false, int PATH = kPathAny, class EV>
 __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, int n, const float4 *pose,
                                                const float4 *cw, int h0, int nh, unsigned *keyh, int ppl,
                                                const float4 *circ, float cap, unsigned *msk, int *pre,
@@ -634,7 +639,7 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
         body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
         body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
     };
-    if (cap < 0.f || (queue_points && !EV::kQueueOk)) {   // no pruning
+    if (PATH == kPathAny && (cap < 0.f || (queue_points && !EV::kQueueOk))) {   // no pruning
         const int span = 32 * 4;   // pairs per item
         const int nchunk = npairs > 0 ? (npairs + span - 1) / span : 0;
         const int items = nh * nchunk;
@@ -682,7 +687,7 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
         }
         return;
     }
-    if constexpr (EV::kQueueOk) if (queue_points) {
+    if constexpr (EV::kQueueOk) if (PATH == kPathPoints || queue_points) {
         // Point-level pruning (clouds below kPruneMin, no sort, no circles).
         // Every warp first bounds the sample's trajectory by one circle
         // (cb, rb) that holds the footprint's bounding circle at every step
@@ -811,283 +816,285 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
         if (qn > 0) flush(qn);
         return;
     }
-    const float brad = ev.bound().z;
-    const float lim = cap >= 0.f ? cap + kPruneSlack : finf();
-    // 1. per (step, sub-chunk) tests, 32 sub-chunks per ballot
-    for (int idx = warp; idx < 2 * nh; idx += nwarps) {
-        const int hh = idx >> 1, s = ((idx & 1) << 5) + lane;
-        bool keep = false;
-        if (s < nsub) {
-            const float4 cc = circ[s];
-            if (cc.z >= 0.f) {
-                const float4 cq = cw[h0 + hh];
-                const float dx = cc.x - cq.x, dy = cc.y - cq.y;
-                float reach = cc.z + brad + 1e-5f * (fabsf(cc.x) + fabsf(cc.y) + fabsf(cq.x) + fabsf(cq.y));
-                if (MOVING) reach = fmaf(cq.z, cc.w, reach);
-                const float far = reach + lim;   // drop iff |centre - footprint centre| > far
-                keep = !(fmaf(dx, dx, dy * dy) > far * far);
-            }
-        }
-        const unsigned b = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) msk[idx] = b;
-    }
-    __syncthreads();
-    // 2. exclusive prefix of the per-step counts
-    if (warp == 0) {
-        int run = 0;
-        for (int base = 0; base < nh; base += 32) {
-            const int hh = base + lane;
-            const int cnt = hh < nh ? __popc(msk[2 * hh]) + __popc(msk[2 * hh + 1]) : 0;
-            int inc = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += t;
-            }
-            if (hh < nh) pre[hh] = run + inc - cnt;
-            run += __shfl_sync(0xffffffffu, inc, 31);
-        }
-        if (lane == 0) pre[nh] = run;
-    }
-    __syncthreads();
-    // 3. this warp's share [e0, e1) of the kept list, in (step, sub-chunk) order
-    const int L = pre[nh];
-    const int e0 = (int)(((long long)L * warp) / nwarps), e1 = (int)(((long long)L * (warp + 1)) / nwarps);
-    if (e0 >= e1) return;
-    int lo = 0, hi = nh - 1;   // the step holding entry e0: the last with pre <= e0
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= e0) lo = mid; else hi = mid - 1;
-    }
-    int hh = lo;
-    unsigned long long m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
-    for (int k = pre[hh]; k < e0; ++k) m &= m - 1ull;
-    if constexpr (EV::kBoxTest) {
-        // Polygons and shared-memory footprints: the points of a kept
-        // sub-chunk are moved into the body frame of its step and kept only
-        // if they lie within cap (plus the slack) of the footprint's bounding
-        // box there; the kept ones go through the warp's queue, as in the
-        // point-level path.  The evaluator gives the same key for that
-        // body-frame point, and sd_F >= sd_box everywhere for a footprint F
-        // inside the box, so a dropped point is provably farther than cap.
-        // (For a rectangle cover the test costs about what the evaluation
-        // does, and the kept points are evaluated directly below.)
-        const float4 fb = ev.box();
-        const int cap_q = kQueueAll / nwarps;
-        const int flush_at = cap_q >= 128 ? 64 : 1;
-        int *q = queue + warp * cap_q;
-        int qn = 0;   // warp-uniform
-        auto point_at = [&](int i, int h) -> float2 {
-            if constexpr (MOVING) {
-                const float th = cw[h].z;
-                const float4 a = reinterpret_cast<const float4 *>(pts)[i];
-                return make_float2(fmaf(th, a.z, a.x), fmaf(th, a.w, a.y));
-            } else {
-                return pts[i];
-            }
-        };
-        int e = e0, jb = 0, jend = 0;
-        for (;;) {
-            if (jb >= jend && e < e1) {   // next kept (step, sub-chunk) entry
-                while (m == 0ull && EXACT_DCHECK(hh + 1 < nh, err)) {
-                    ++hh;
-                    m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
-                }
-                if (m == 0ull) {   // debug build: the list ended early
-                    e = e1;
-                } else {
-                    const int s = __ffsll((long long)m) - 1;
-                    m &= m - 1ull;
-                    ++e;
-                    jb = s * 32 * ppl;
-                    jend = min(npairs, (s + 1) * 32 * ppl);
-                }
-            }
-            const bool more = jb < jend;
-            const int j = jb + lane;   // points 2j and 2j + 1 of step slot hh
-            bool k0 = false, k1 = false;
-            if (more && j < jend) {
-                const float4 qp = pose[h0 + hh];
-                auto near_box = [&](float2 o) {
-                    float px, py;
-                    body_frame(o.x, o.y, qp.x, qp.y, qp.z, qp.w, px, py);
-                    const float ax = fabsf(px - fb.x) - fb.z, ay = fabsf(py - fb.y) - fb.w;
-                    const float l = fmaf(1e-5f, fabsf(px) + fabsf(py), lim);
-                    const float mx = fmaxf(ax, 0.f), my = fmaxf(ay, 0.f);
-                    return ax <= l && ay <= l && fmaf(mx, mx, my * my) <= l * l;   // NaN (masked): false
-                };
-                k0 = near_box(point_at(2 * j, h0 + hh));
-                if (2 * j + 1 < n) k1 = near_box(point_at(2 * j + 1, h0 + hh));
-            }
-            jb += 32;
-            const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
-            if (b0 | b1) {
-                const unsigned below = (1u << lane) - 1u;
-                const int pos = qn + __popc(b0 & below) + __popc(b1 & below);
-                if (k0) q[pos] = (hh << 12) | (2 * j);
-                if (k1) q[pos + (k0 ? 1 : 0)] = (hh << 12) | (2 * j + 1);
-                qn += __popc(b0) + __popc(b1);
-            }
-            if (qn >= flush_at || (!more && qn > 0)) {
-                // evaluate entries [0, f), f <= 64, and move the rest to the front
-                const int f = min(qn, 64);
-                __syncwarp();
-                const int a = 2 * lane;
-                if (a < f) {
-                    const bool two = a + 1 < f;
-                    int ea = q[a], eb = two ? q[a + 1] : ea;
-                    if (!EXACT_DCHECK((ea & 4095) < n && (ea >> 12) < nh, err)) ea = 0;   // debug build: skip
-                    if (!EXACT_DCHECK((eb & 4095) < n && (eb >> 12) < nh, err)) eb = 0;
-                    const int ha = h0 + (ea >> 12), hb = h0 + (eb >> 12);
-                    const float2 oa = point_at(ea & 4095, ha), ob = point_at(eb & 4095, hb);
-                    const float4 pa = pose[ha], pb = pose[hb];
-                    float pxa, pya, pxb, pyb;
-                    body_frame(oa.x, oa.y, pa.x, pa.y, pa.z, pa.w, pxa, pya);
-                    body_frame(ob.x, ob.y, pb.x, pb.y, pb.z, pb.w, pxb, pyb);
-                    float ka, kb;
-                    ev.eval2(pxa, pya, pxb, pyb, ka, kb);
-                    atomicMin(keyh + ha, f2ord(ka));
-                    if (two) atomicMin(keyh + hb, f2ord(kb));
-                }
-                __syncwarp();
-                for (int i = lane; i < qn - f; i += 32) q[i] = q[f + i];
-                __syncwarp();
-                qn -= f;
-            }
-            if (!more && qn == 0) return;
-        }
-    }
-    if (circf) {
-        // Rectangle covers with the fine circles of an ordered cloud: the
-        // four 16-point fine sub-chunks of every kept (step, sub-chunk) entry
-        // are tested against the footprint's bounding box in the step's body
-        // frame (one lane per fine sub-chunk, eight entries per warp
-        // iteration, each lane decoding its own entry from pre and msk); the
-        // kept ones go through the warp's queue and are evaluated four at a
-        // time, eight lanes (one pair each) per fine sub-chunk, whose step
-        // minimum is folded over the eight lanes and into keyh[h] with one
-        // shared atomicMin.  Every point of a fine sub-chunk lies within its
-        // circle (radius grown by t_h times its largest speed when MOVING),
-        // sd_F >= sd_box for a footprint F inside the box, and sd_box is
-        // 1-Lipschitz, so a dropped fine sub-chunk holds no point within cap.
-        const float4 fb = ev.box();
-        const int capf = kQueueFine / nwarps;   // >= 40 for up to 16 warps: 3 left + 32 added fit
-        int *q = qfine + warp * capf;
-        int qn = 0;   // warp-uniform
-        const int nfine = (n + kFine - 1) / kFine;
-        for (int e = e0;; e += 8) {
-            const bool more = e < e1;
-            const int my = e + (lane >> 2);
+    if constexpr (PATH == kPathAny) {
+        const float brad = ev.bound().z;
+        const float lim = cap >= 0.f ? cap + kPruneSlack : finf();
+        // 1. per (step, sub-chunk) tests, 32 sub-chunks per ballot
+        for (int idx = warp; idx < 2 * nh; idx += nwarps) {
+            const int hh = idx >> 1, s = ((idx & 1) << 5) + lane;
             bool keep = false;
-            int code = 0;
-            if (more && my < e1) {
-                int lo = 0, hi = nh - 1;   // the step holding entry my: the last with pre <= my
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (pre[mid] <= my) lo = mid; else hi = mid - 1;
+            if (s < nsub) {
+                const float4 cc = circ[s];
+                if (cc.z >= 0.f) {
+                    const float4 cq = cw[h0 + hh];
+                    const float dx = cc.x - cq.x, dy = cc.y - cq.y;
+                    float reach = cc.z + brad + 1e-5f * (fabsf(cc.x) + fabsf(cc.y) + fabsf(cq.x) + fabsf(cq.y));
+                    if (MOVING) reach = fmaf(cq.z, cc.w, reach);
+                    const float far = reach + lim;   // drop iff |centre - footprint centre| > far
+                    keep = !(fmaf(dx, dx, dy * dy) > far * far);
                 }
-                const unsigned long long mm = ((unsigned long long)msk[2 * lo + 1] << 32) | msk[2 * lo];
-                const int fi = nth_set_bit64(mm, my - pre[lo]) * (kSub / kFine) + (lane & 3);
-                if (fi < nfine) {
-                    const float4 c = circf[fi];
-                    if (c.z >= 0.f) {
-                        const float4 qp = pose[h0 + lo];
-                        float px, py;
-                        body_frame(c.x, c.y, qp.x, qp.y, qp.z, qp.w, px, py);
-                        float reach = c.z + 1e-5f * (fabsf(c.x) + fabsf(c.y) + fabsf(qp.x) + fabsf(qp.y));
-                        if (MOVING) reach = fmaf(cw[h0 + lo].z, c.w, reach);
-                        const float l = reach + lim;
-                        const float ax = fabsf(px - fb.x) - fb.z, ay = fabsf(py - fb.y) - fb.w;
-                        const float mx = fmaxf(ax, 0.f), my2 = fmaxf(ay, 0.f);
-                        keep = ax <= l && ay <= l && fmaf(mx, mx, my2 * my2) <= l * l;
-                    }
-                }
-                code = (lo << 12) | fi;
             }
             const unsigned b = __ballot_sync(0xffffffffu, keep);
-            if (keep) q[qn + __popc(b & ((1u << lane) - 1u))] = code;
-            qn += __popc(b);
-            while (qn >= 4 || (!more && qn > 0)) {
-                // evaluate entries [0, f), f <= 4, and move the rest to the front
-                const int f = min(qn, 4);
-                __syncwarp();
-                const int slot = lane >> 3, pr = lane & 7;
-                float best = finf();
-                int sh = 0;
-                if (slot < f) {
-                    int ce = q[slot];
-                    if (!EXACT_DCHECK((ce >> 12) < nh && (ce & 4095) < nfine, err)) ce = 0;   // debug build: skip
-                    sh = ce >> 12;
-                    const int j = (ce & 4095) * (kFine / 2) + pr;   // pair j of the staged points
-                    if (j < npairs) {
-                        const int h = h0 + sh;
-                        const float4 qp = pose[h];
-                        float2 o0, o1;
-                        if constexpr (MOVING) {
-                            const float th = cw[h].z;
-                            const float4 *p4 = reinterpret_cast<const float4 *>(pts);
-                            const float4 a0 = p4[2 * j], a1 = p4[min(2 * j + 1, n - 1)];
-                            o0 = make_float2(fmaf(th, a0.z, a0.x), fmaf(th, a0.w, a0.y));
-                            o1 = make_float2(fmaf(th, a1.z, a1.x), fmaf(th, a1.w, a1.y));
-                        } else {
-                            o0 = pts[2 * j];
-                            o1 = pts[min(2 * j + 1, n - 1)];
-                        }
-                        float px0, py0, px1, py1;
-                        body_frame(o0.x, o0.y, qp.x, qp.y, qp.z, qp.w, px0, py0);
-                        body_frame(o1.x, o1.y, qp.x, qp.y, qp.z, qp.w, px1, py1);
-                        float k0, k1;
-                        ev.eval2(px0, py0, px1, py1, k0, k1);
-                        best = fminf(k0, k1);
+            if (lane == 0) msk[idx] = b;
+        }
+        __syncthreads();
+        // 2. exclusive prefix of the per-step counts
+        if (warp == 0) {
+            int run = 0;
+            for (int base = 0; base < nh; base += 32) {
+                const int hh = base + lane;
+                const int cnt = hh < nh ? __popc(msk[2 * hh]) + __popc(msk[2 * hh + 1]) : 0;
+                int inc = cnt;
+    #pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += t;
+                }
+                if (hh < nh) pre[hh] = run + inc - cnt;
+                run += __shfl_sync(0xffffffffu, inc, 31);
+            }
+            if (lane == 0) pre[nh] = run;
+        }
+        __syncthreads();
+        // 3. this warp's share [e0, e1) of the kept list, in (step, sub-chunk) order
+        const int L = pre[nh];
+        const int e0 = (int)(((long long)L * warp) / nwarps), e1 = (int)(((long long)L * (warp + 1)) / nwarps);
+        if (e0 >= e1) return;
+        int lo = 0, hi = nh - 1;   // the step holding entry e0: the last with pre <= e0
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= e0) lo = mid; else hi = mid - 1;
+        }
+        int hh = lo;
+        unsigned long long m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
+        for (int k = pre[hh]; k < e0; ++k) m &= m - 1ull;
+        if constexpr (EV::kBoxTest) {
+            // Polygons and shared-memory footprints: the points of a kept
+            // sub-chunk are moved into the body frame of its step and kept only
+            // if they lie within cap (plus the slack) of the footprint's bounding
+            // box there; the kept ones go through the warp's queue, as in the
+            // point-level path.  The evaluator gives the same key for that
+            // body-frame point, and sd_F >= sd_box everywhere for a footprint F
+            // inside the box, so a dropped point is provably farther than cap.
+            // (For a rectangle cover the test costs about what the evaluation
+            // does, and the kept points are evaluated directly below.)
+            const float4 fb = ev.box();
+            const int cap_q = kQueueAll / nwarps;
+            const int flush_at = cap_q >= 128 ? 64 : 1;
+            int *q = queue + warp * cap_q;
+            int qn = 0;   // warp-uniform
+            auto point_at = [&](int i, int h) -> float2 {
+                if constexpr (MOVING) {
+                    const float th = cw[h].z;
+                    const float4 a = reinterpret_cast<const float4 *>(pts)[i];
+                    return make_float2(fmaf(th, a.z, a.x), fmaf(th, a.w, a.y));
+                } else {
+                    return pts[i];
+                }
+            };
+            int e = e0, jb = 0, jend = 0;
+            for (;;) {
+                if (jb >= jend && e < e1) {   // next kept (step, sub-chunk) entry
+                    while (m == 0ull && EXACT_DCHECK(hh + 1 < nh, err)) {
+                        ++hh;
+                        m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
+                    }
+                    if (m == 0ull) {   // debug build: the list ended early
+                        e = e1;
+                    } else {
+                        const int s = __ffsll((long long)m) - 1;
+                        m &= m - 1ull;
+                        ++e;
+                        jb = s * 32 * ppl;
+                        jend = min(npairs, (s + 1) * 32 * ppl);
                     }
                 }
-#pragma unroll
-                for (int o = 4; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
-                if (slot < f && pr == 0 && best < finf()) atomicMin(keyh + h0 + sh, f2ord(best));
-                __syncwarp();
-                for (int i = lane; i < qn - f; i += 32) q[i] = q[f + i];
-                __syncwarp();
-                qn -= f;
+                const bool more = jb < jend;
+                const int j = jb + lane;   // points 2j and 2j + 1 of step slot hh
+                bool k0 = false, k1 = false;
+                if (more && j < jend) {
+                    const float4 qp = pose[h0 + hh];
+                    auto near_box = [&](float2 o) {
+                        float px, py;
+                        body_frame(o.x, o.y, qp.x, qp.y, qp.z, qp.w, px, py);
+                        const float ax = fabsf(px - fb.x) - fb.z, ay = fabsf(py - fb.y) - fb.w;
+                        const float l = fmaf(1e-5f, fabsf(px) + fabsf(py), lim);
+                        const float mx = fmaxf(ax, 0.f), my = fmaxf(ay, 0.f);
+                        return ax <= l && ay <= l && fmaf(mx, mx, my * my) <= l * l;   // NaN (masked): false
+                    };
+                    k0 = near_box(point_at(2 * j, h0 + hh));
+                    if (2 * j + 1 < n) k1 = near_box(point_at(2 * j + 1, h0 + hh));
+                }
+                jb += 32;
+                const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
+                if (b0 | b1) {
+                    const unsigned below = (1u << lane) - 1u;
+                    const int pos = qn + __popc(b0 & below) + __popc(b1 & below);
+                    if (k0) q[pos] = (hh << 12) | (2 * j);
+                    if (k1) q[pos + (k0 ? 1 : 0)] = (hh << 12) | (2 * j + 1);
+                    qn += __popc(b0) + __popc(b1);
+                }
+                if (qn >= flush_at || (!more && qn > 0)) {
+                    // evaluate entries [0, f), f <= 64, and move the rest to the front
+                    const int f = min(qn, 64);
+                    __syncwarp();
+                    const int a = 2 * lane;
+                    if (a < f) {
+                        const bool two = a + 1 < f;
+                        int ea = q[a], eb = two ? q[a + 1] : ea;
+                        if (!EXACT_DCHECK((ea & 4095) < n && (ea >> 12) < nh, err)) ea = 0;   // debug build: skip
+                        if (!EXACT_DCHECK((eb & 4095) < n && (eb >> 12) < nh, err)) eb = 0;
+                        const int ha = h0 + (ea >> 12), hb = h0 + (eb >> 12);
+                        const float2 oa = point_at(ea & 4095, ha), ob = point_at(eb & 4095, hb);
+                        const float4 pa = pose[ha], pb = pose[hb];
+                        float pxa, pya, pxb, pyb;
+                        body_frame(oa.x, oa.y, pa.x, pa.y, pa.z, pa.w, pxa, pya);
+                        body_frame(ob.x, ob.y, pb.x, pb.y, pb.z, pb.w, pxb, pyb);
+                        float ka, kb;
+                        ev.eval2(pxa, pya, pxb, pyb, ka, kb);
+                        atomicMin(keyh + ha, f2ord(ka));
+                        if (two) atomicMin(keyh + hb, f2ord(kb));
+                    }
+                    __syncwarp();
+                    for (int i = lane; i < qn - f; i += 32) q[i] = q[f + i];
+                    __syncwarp();
+                    qn -= f;
+                }
+                if (!more && qn == 0) return;
             }
-            if (!more) return;
         }
-    }
-    float best = finf();
-    for (int e = e0; e < e1; ++e) {
-        if (!EXACT_DCHECK(hh < nh, err)) break;
-        while (m == 0ull) {   // step done: fold its minimum, move to the next step with entries
-            best = warp_min_f(best);
-            if (lane == 0 && best < finf()) atomicMin(keyh + h0 + hh, f2ord(best));
-            best = finf();
-            ++hh;
-            m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
-        }
-        const int s = __ffsll((long long)m) - 1;
-        m &= m - 1ull;
-        const int h = h0 + hh;
-        const float4 q = pose[h];
-        const float th = cw[h].z;
-        for (int j = s * 32 * ppl + lane; j < min(npairs, (s + 1) * 32 * ppl); j += 32) {
-            float2 o0, o1;
-            if constexpr (MOVING) {
-                const float4 *p4 = reinterpret_cast<const float4 *>(pts);
-                const float4 a0 = p4[2 * j], a1 = p4[min(2 * j + 1, n - 1)];
-                o0 = make_float2(fmaf(th, a0.z, a0.x), fmaf(th, a0.w, a0.y));
-                o1 = make_float2(fmaf(th, a1.z, a1.x), fmaf(th, a1.w, a1.y));
-            } else {
-                o0 = pts[2 * j];
-                o1 = pts[min(2 * j + 1, n - 1)];
+        if (circf) {
+            // Rectangle covers with the fine circles of an ordered cloud: the
+            // four 16-point fine sub-chunks of every kept (step, sub-chunk) entry
+            // are tested against the footprint's bounding box in the step's body
+            // frame (one lane per fine sub-chunk, eight entries per warp
+            // iteration, each lane decoding its own entry from pre and msk); the
+            // kept ones go through the warp's queue and are evaluated four at a
+            // time, eight lanes (one pair each) per fine sub-chunk, whose step
+            // minimum is folded over the eight lanes and into keyh[h] with one
+            // shared atomicMin.  Every point of a fine sub-chunk lies within its
+            // circle (radius grown by t_h times its largest speed when MOVING),
+            // sd_F >= sd_box for a footprint F inside the box, and sd_box is
+            // 1-Lipschitz, so a dropped fine sub-chunk holds no point within cap.
+            const float4 fb = ev.box();
+            const int capf = kQueueFine / nwarps;   // >= 40 for up to 16 warps: 3 left + 32 added fit
+            int *q = qfine + warp * capf;
+            int qn = 0;   // warp-uniform
+            const int nfine = (n + kFine - 1) / kFine;
+            for (int e = e0;; e += 8) {
+                const bool more = e < e1;
+                const int my = e + (lane >> 2);
+                bool keep = false;
+                int code = 0;
+                if (more && my < e1) {
+                    int lo = 0, hi = nh - 1;   // the step holding entry my: the last with pre <= my
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (pre[mid] <= my) lo = mid; else hi = mid - 1;
+                    }
+                    const unsigned long long mm = ((unsigned long long)msk[2 * lo + 1] << 32) | msk[2 * lo];
+                    const int fi = nth_set_bit64(mm, my - pre[lo]) * (kSub / kFine) + (lane & 3);
+                    if (fi < nfine) {
+                        const float4 c = circf[fi];
+                        if (c.z >= 0.f) {
+                            const float4 qp = pose[h0 + lo];
+                            float px, py;
+                            body_frame(c.x, c.y, qp.x, qp.y, qp.z, qp.w, px, py);
+                            float reach = c.z + 1e-5f * (fabsf(c.x) + fabsf(c.y) + fabsf(qp.x) + fabsf(qp.y));
+                            if (MOVING) reach = fmaf(cw[h0 + lo].z, c.w, reach);
+                            const float l = reach + lim;
+                            const float ax = fabsf(px - fb.x) - fb.z, ay = fabsf(py - fb.y) - fb.w;
+                            const float mx = fmaxf(ax, 0.f), my2 = fmaxf(ay, 0.f);
+                            keep = ax <= l && ay <= l && fmaf(mx, mx, my2 * my2) <= l * l;
+                        }
+                    }
+                    code = (lo << 12) | fi;
+                }
+                const unsigned b = __ballot_sync(0xffffffffu, keep);
+                if (keep) q[qn + __popc(b & ((1u << lane) - 1u))] = code;
+                qn += __popc(b);
+                while (qn >= 4 || (!more && qn > 0)) {
+                    // evaluate entries [0, f), f <= 4, and move the rest to the front
+                    const int f = min(qn, 4);
+                    __syncwarp();
+                    const int slot = lane >> 3, pr = lane & 7;
+                    float best = finf();
+                    int sh = 0;
+                    if (slot < f) {
+                        int ce = q[slot];
+                        if (!EXACT_DCHECK((ce >> 12) < nh && (ce & 4095) < nfine, err)) ce = 0;   // debug build: skip
+                        sh = ce >> 12;
+                        const int j = (ce & 4095) * (kFine / 2) + pr;   // pair j of the staged points
+                        if (j < npairs) {
+                            const int h = h0 + sh;
+                            const float4 qp = pose[h];
+                            float2 o0, o1;
+                            if constexpr (MOVING) {
+                                const float th = cw[h].z;
+                                const float4 *p4 = reinterpret_cast<const float4 *>(pts);
+                                const float4 a0 = p4[2 * j], a1 = p4[min(2 * j + 1, n - 1)];
+                                o0 = make_float2(fmaf(th, a0.z, a0.x), fmaf(th, a0.w, a0.y));
+                                o1 = make_float2(fmaf(th, a1.z, a1.x), fmaf(th, a1.w, a1.y));
+                            } else {
+                                o0 = pts[2 * j];
+                                o1 = pts[min(2 * j + 1, n - 1)];
+                            }
+                            float px0, py0, px1, py1;
+                            body_frame(o0.x, o0.y, qp.x, qp.y, qp.z, qp.w, px0, py0);
+                            body_frame(o1.x, o1.y, qp.x, qp.y, qp.z, qp.w, px1, py1);
+                            float k0, k1;
+                            ev.eval2(px0, py0, px1, py1, k0, k1);
+                            best = fminf(k0, k1);
+                        }
+                    }
+    #pragma unroll
+                    for (int o = 4; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+                    if (slot < f && pr == 0 && best < finf()) atomicMin(keyh + h0 + sh, f2ord(best));
+                    __syncwarp();
+                    for (int i = lane; i < qn - f; i += 32) q[i] = q[f + i];
+                    __syncwarp();
+                    qn -= f;
+                }
+                if (!more) return;
             }
-            float px0, py0, px1, py1;
-            body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
-            body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
-            float k0, k1;
-            ev.eval2(px0, py0, px1, py1, k0, k1);
-            best = fmin3(best, k0, k1);
         }
+        float best = finf();
+        for (int e = e0; e < e1; ++e) {
+            if (!EXACT_DCHECK(hh < nh, err)) break;
+            while (m == 0ull) {   // step done: fold its minimum, move to the next step with entries
+                best = warp_min_f(best);
+                if (lane == 0 && best < finf()) atomicMin(keyh + h0 + hh, f2ord(best));
+                best = finf();
+                ++hh;
+                m = ((unsigned long long)msk[2 * hh + 1] << 32) | msk[2 * hh];
+            }
+            const int s = __ffsll((long long)m) - 1;
+            m &= m - 1ull;
+            const int h = h0 + hh;
+            const float4 q = pose[h];
+            const float th = cw[h].z;
+            for (int j = s * 32 * ppl + lane; j < min(npairs, (s + 1) * 32 * ppl); j += 32) {
+                float2 o0, o1;
+                if constexpr (MOVING) {
+                    const float4 *p4 = reinterpret_cast<const float4 *>(pts);
+                    const float4 a0 = p4[2 * j], a1 = p4[min(2 * j + 1, n - 1)];
+                    o0 = make_float2(fmaf(th, a0.z, a0.x), fmaf(th, a0.w, a0.y));
+                    o1 = make_float2(fmaf(th, a1.z, a1.x), fmaf(th, a1.w, a1.y));
+                } else {
+                    o0 = pts[2 * j];
+                    o1 = pts[min(2 * j + 1, n - 1)];
+                }
+                float px0, py0, px1, py1;
+                body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
+                body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
+                float k0, k1;
+                ev.eval2(px0, py0, px1, py1, k0, k1);
+                best = fmin3(best, k0, k1);
+            }
+        }
+        best = warp_min_f(best);
+        if (lane == 0 && best < finf()) atomicMin(keyh + h0 + hh, f2ord(best));
     }
-    best = warp_min_f(best);
-    if (lane == 0 && best < finf()) atomicMin(keyh + h0 + hh, f2ord(best));
 }
 
 // Copy points [base, base + n) into shared memory, masked ones as NaN, with
@@ -1260,7 +1267,7 @@ __device__ __forceinline__ void sample_smem_init(SampleSmem &sm) {
 // s T + h), one pass over the staged points serves both, and warps 0 and 1
 // form the two J~.  Each sample's J~ takes exactly the operations of the
 // one-sample path.
-template <bool MOVING = false, class EV>
+template <bool MOVING = false, int PATH = kPathAny, class EV>
 __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, int r, int p, SampleSmem &sm,
                                             float2 *s_pts, bool staged, int pairs_per_lane,
                                             const float4 *circ = nullptr, int r2 = -1) {
@@ -1308,7 +1315,7 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
                                  &sm.bar_uses, V.err);
     }
     __syncthreads();
-    const bool prune = !V.dmin && N >= kPruneMin;
+    const bool prune = PATH == kPathAny && !V.dmin && N >= kPruneMin;
     // sub-chunk circles: copied from the ordered cloud's (64-point sub-chunks),
     // or computed from the staged points
     const bool pre_circ = circ != nullptr && pairs_per_lane == 1;
@@ -1329,9 +1336,10 @@ __device__ __forceinline__ void sample_body(const SceneView &V, const EV &ev, in
     // sub-chunks (clouds of kPruneMin points or more) or far points (smaller
     // clouds, one pass) are skipped
     const float cap = V.dmin ? -1.f : fmaxf(P.d_safe, 0.f);
-    steps_min_keys<MOVING>(ev, s_pts, n0, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
-                           sm.pre, sm.queue, !V.dmin && N < kPruneMin, fine ? sm.circf : nullptr, sm.qfine, V.err);
-    for (int base = kS; base < N; base += kS) {   // clouds larger than the stage
+    steps_min_keys<MOVING, PATH>(ev, s_pts, n0, sm.pose, sm.cw, k0, nk, sm.key, pairs_per_lane, sm.circ, cap, sm.msk,
+                                 sm.pre, sm.queue, !V.dmin && N < kPruneMin, fine ? sm.circf : nullptr, sm.qfine,
+                                 V.err);
+    if constexpr (PATH == kPathAny) for (int base = kS; base < N; base += kS) {   // clouds larger than the stage
         const int n = min(kS, N - base);
         __syncthreads();
         stage_points<MOVING>(s_pts, V.pts, V.vel, V.mask, base, n, threadIdx.x, blockDim.x, &sm.bar, &sm.bar_uses,

@@ -14,7 +14,7 @@
 
 namespace exact {
 
-template <class FPC, bool MOVING, int MINB>
+template <class FPC, bool MOVING, int MINB, int PATH>
 __global__ void __launch_bounds__(kBlock, MINB)
 mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev, const float4 *circ, int pair) {
     extern __shared__ float2 s_pts[];   // min(N, stage) staged points (float4 each when MOVING)
@@ -34,7 +34,7 @@ mppi_sample_kernel(const SceneView V, const ConstEval<FPC> ev, const float4 *cir
     const bool two = MINB != 0 && !MOVING && pair;
     const int r = two ? 2 * (int)blockIdx.x : (int)blockIdx.x / V.parts;
     const int p = two ? 0 : (int)blockIdx.x % V.parts;
-    sample_body<MOVING>(V, ev, r, p, sm, s_pts, false, 1, circ, two && r + 1 < V.P.K ? r + 1 : -1);
+    sample_body<MOVING, PATH>(V, ev, r, p, sm, s_pts, false, 1, circ, two && r + 1 < V.P.K ? r + 1 : -1);
 }
 
 template <bool MOVING>
@@ -74,21 +74,24 @@ inline size_t cloud_copy_bytes(int N, bool moving) {
 // The three launches of one cycle for a scene whose scratch is carved.
 // pdl: the sample kernel follows a cloud-ordering kernel and may start early
 // (its rollouts do not read the cloud; sample_body waits before staging).
-template <bool MOVING, int MINB>
+// PATH = kPathPoints: only for footprints whose evaluator prunes point by
+// point (ConstEval::kQueueOk), cycles without a d_min output and clouds below
+// kPruneMin points.
+template <bool MOVING, int MINB, int PATH = kPathAny>
 int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
                    int sms) {
     const size_t smem = (size_t)min(V.N, stage_points_of<MOVING>()) * (MOVING ? sizeof(float4) : sizeof(float2));
     const int pair = MINB != 0 && !MOVING ? pair_samples(V.P.K, V.P.T, V.parts, sms) : 0;
     const int grid = pair ? (V.P.K + 1) / 2 : V.P.K * V.parts;
-    return with_footprint(fp, [&](auto fpc) -> int {
+    auto launch = [&](auto fpc) -> int {
         using FPC = decltype(fpc);
         const ConstEval<FPC> ev{fpc};
         if (pdl) {
-            if (launch_dependent(mppi_sample_kernel<FPC, MOVING, MINB>, grid, kBlock, smem, st, V, ev, circ, pair) !=
-                cudaSuccess)
+            if (launch_dependent(mppi_sample_kernel<FPC, MOVING, MINB, PATH>, grid, kBlock, smem, st, V, ev, circ,
+                                 pair) != cudaSuccess)
                 return EXACT_ECUDA;
         } else {
-            mppi_sample_kernel<FPC, MOVING, MINB><<<grid, kBlock, smem, st>>>(V, ev, circ, pair);
+            mppi_sample_kernel<FPC, MOVING, MINB, PATH><<<grid, kBlock, smem, st>>>(V, ev, circ, pair);
             if (cudaGetLastError() != cudaSuccess) return EXACT_ECUDA;
         }
         if (launch_dependent(mppi_update_kernel<MOVING>, V.upd_blocks, kUpdBlock, 0, st, V) != cudaSuccess)
@@ -97,10 +100,14 @@ int launch_cycle_t(const SceneView &V, const exact_footprint *fp, cudaStream_t s
             cudaSuccess)
             return EXACT_ECUDA;
         return EXACT_OK;
-    });
+    };
+    if constexpr (PATH == kPathPoints)
+        return with_small_footprint(fp, launch);
+    else
+        return with_footprint(fp, launch);
 }
 
-// Any cycle (mppi.cu: picks one of the three below), the static capped cycle
+// Any cycle (mppi.cu: picks one of the four below), the static capped cycle
 // (mppi_dense.cu) and the predicted cycle (mppi_predicted.cu).  sms is the
 // SM count of the device the cycle runs on (it sizes the grids).
 int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
@@ -108,6 +115,10 @@ int launch_cycle(const SceneView &V, const exact_footprint *fp, cudaStream_t st,
 int launch_cycle_dense(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
                        int sms);
 int launch_cycle_moving(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
+                        int sms);
+// The static capped cycle whose sample kernel holds only the point-level
+// pruning (mppi_points.cu): small footprints, no d_min output, N < kPruneMin.
+int launch_cycle_points(const SceneView &V, const exact_footprint *fp, cudaStream_t st, bool pdl, const float4 *circ,
                         int sms);
 
 // mppi_step with optional point velocities (NULL: static cloud).
