@@ -578,7 +578,7 @@ def batched_small_extra(torch, ex, dev, n_scenes=128, steps=5):
     return out
 
 
-def learned_extra(torch, ex, dev, samples=20000, episodes=32, max_steps=150):
+def learned_extra(torch, ex, dev, samples=50000, episodes=128, max_steps=250):
     """The learned sampling proposal at reduced scale: closed-loop plain MPPI
     (K = 4096) data in 64 guided worlds, a few epochs of training on the
     tensor-core MLP kernels, then held-out worlds (the same for every method)

@@ -402,8 +402,8 @@ def evaluate(torch, dev, method: str, K: int, n_episodes: int, seed: int, mlp: M
     """Closed-loop episodes on seeded held-out worlds (the same worlds for
     every method).  Final trajectory cost = sum over executed steps of
     w_goal |p - g| + w_ctrl |u|^2 + phi_obs(d), d the exact clearance of the
-    executed pose; after a collision the robot stays put and every remaining
-    step adds w_coll + the goal term."""
+    executed pose (a collision step pays w_coll); a collided robot stays put
+    and pays the goal term for every step of the episode it did not run."""
     fp = Footprint.polygon(synth.l_footprint())
     world = World(n_episodes, seed, max_steps, **(world_kw or {}))
     if method == "plain":
@@ -418,6 +418,7 @@ def evaluate(torch, dev, method: str, K: int, n_episodes: int, seed: int, mlp: M
     success = np.zeros(n_episodes, bool)
     collided = np.zeros(n_episodes, bool)
     t_goal = np.full(n_episodes, max_steps)
+    t_coll = np.full(n_episodes, max_steps)
     cost = np.zeros(n_episodes)
     chose = []
     best_gap = []      # per active step: min J~ of the plain candidate - min J~ of the kept one
@@ -443,15 +444,15 @@ def evaluate(torch, dev, method: str, K: int, n_episodes: int, seed: int, mlp: M
         cost += np.where(active, c, 0.0)
         newly_coll = active & (d < 0)
         collided |= newly_coll
+        t_coll = np.where(newly_coll, step + 1, t_coll)
         reached = active & (world.goal_dist() < GOAL_TOL)
         success |= reached
         t_goal = np.where(reached, step + 1, t_goal)
         active &= ~(newly_coll | reached)
         if not active.any():
             break
-    # collided episodes pay w_coll + the goal term for every step they did not complete
-    rem = max_steps - (step + 1)
-    cost += np.where(collided, (p["w_coll"] + p["w_goal"] * world.goal_dist()) * rem, 0.0)
+    # a collided robot stays where it collided: the goal term for every step it did not run
+    cost += np.where(collided, p["w_goal"] * world.goal_dist() * (max_steps - t_coll), 0.0)
     ci = 1.96 * cost.std(ddof=1) / math.sqrt(n_episodes)
     progress = np.hypot(world.goal[:, 0], world.goal[:, 1]) - world.goal_dist()
     res = {"method": method, "K": K, "episodes": n_episodes, "cost_mean": float(cost.mean()), "cost_ci95": float(ci),

@@ -272,6 +272,37 @@ def test_pruning_edge_cases(ex, ctx, K, T, N, tail):
         compare(s, b, o, check_dmin=False)
 
 
+def _rect_cover(boxes):
+    """Rectangle covers of 1, 3 (the forklift's, at half size) or 8 boxes."""
+    if boxes == 1:
+        return np.array([(0.1, 0.0, 0.5, 0.3)], np.float32)
+    if boxes == 3:
+        return synth.forklift_rects() * np.float32(0.5)
+    xs = np.arange(8, dtype=np.float32)
+    return np.stack([0.15 * xs - 0.5, 0.1 * np.sin(xs), np.full(8, 0.12), 0.1 + 0.02 * xs], 1).astype(np.float32)
+
+
+@pytest.mark.parametrize("K,T,N,tail,boxes", [(256, 20, 1031, 5, 3), (300, 16, 9000, 0, 3), (24, 16, 5000, 3, 1),
+                                              (700, 20, 2048, 0, 8), (512, 12, 4096, 4030, 3)])
+def test_fine_subchunk_pruning_rect_covers(ex, ctx, K, T, N, tail, boxes):
+    """Rectangle covers test the 16-point fine sub-chunks of every kept
+    sub-chunk against the footprint's bounding box: a ragged last fine
+    sub-chunk with a masked tail, several shared-memory passes, a split
+    horizon, two samples per block with an 8-box cover, and sub-chunks of
+    masked points only.  Bitwise against the run with a d_min output (no
+    pruning), and against the oracle."""
+    s = _coherent_scene(K + N + boxes, K, T, N, mask_tail=tail)
+    s["kind"], s["fp"] = synth.RECTS, _rect_cover(boxes)
+    a = run_gpu(ex, ctx, s, dmin=True)
+    b = run_gpu(ex, ctx, s, dmin=False)
+    for k in ("costs", "weights", "U_upd", "U", "u_star"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    assert a["valid"] == b["valid"]
+    o = run_oracle(s)
+    if o["n_near"] == 0:
+        compare(s, b, o, check_dmin=False)
+
+
 def test_largest_sample_count(ex, ctx):
     """K = 65,536 (the largest accepted) against the oracle."""
     s = synth.plain_step(77, K=65536, T=6, N=96)

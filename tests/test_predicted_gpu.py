@@ -138,6 +138,25 @@ def test_pruning_with_predictions_changes_no_cost(ex, ctx):
         np.testing.assert_array_equal(res[0][k], res[1][k], err_msg=k)
 
 
+def test_pruning_with_predictions_rect_cover(ex, ctx):
+    """A rectangle cover with predicted points prunes through the fine
+    sub-chunks (circles grown by t_h * max speed) and the bounding box: the
+    run without a d_min output equals the run with it bit for bit."""
+    import torch
+    s = synth.dynamic_scene(19, K=320, T=20, N=3000, speed=1.5)
+    s["kind"], s["fp"] = synth.RECTS, synth.forklift_rects() * np.float32(0.5)
+    res = []
+    for dmin in (True, False):
+        fp = ex.Footprint(s["kind"], s["fp"])
+        U = _t(s["U"].astype(np.float32))
+        out = ex.mppi_step(ctx, _t(s["q0"]), _t(s["cloud"]), _t(s["waypoints"]), U, _t(s["eps"]), fp, s["params"],
+                           mask=None if s["mask"] is None else _t(s["mask"]), velocity=_t(s["vel"]), dmin=dmin)
+        torch.cuda.synchronize()
+        res.append(dict({k: v.cpu().numpy() for k, v in out.items()}, U=U.cpu().numpy()))
+    for k in ("costs", "weights", "U_upd", "U", "u_star", "valid"):
+        np.testing.assert_array_equal(res[0][k], res[1][k], err_msg=k)
+
+
 def test_predicted_cloud_order_changes_nothing(ex, ctx):
     """Points and velocities shuffled together give the same bits (the cycle
     orders the cloud itself before pruning)."""
