@@ -256,7 +256,8 @@ def mppi_extra(torch, ex, dev, cpu: bool = True):
     out = {}
     ctx = ex.Context()
     for name, make, iters in (("plain_step", lambda: synth.plain_step(0), 2000),
-                              ("forklift", lambda: synth.forklift(0), 200)):
+                              ("forklift", lambda: synth.forklift(0), 200),
+                              ("paper_budget", lambda: synth.paper_budget(0), 1000)):
         s = make()
         p = s["params"]
         fp = ex.Footprint(s["kind"], s["fp"])
@@ -700,7 +701,8 @@ def run_mppi_workload(args):
 def mppi_summary(extra: dict) -> dict:
     """The headline figures of the MPPI cycle measurements in `extra`."""
     out = {}
-    for key, name in (("plain_step", "plain_K256_T20_N512"), ("forklift", "forklift_K2048_T40_N4096")):
+    for key, name in (("plain_step", "plain_K256_T20_N512"), ("forklift", "forklift_K2048_T40_N4096"),
+                      ("paper_budget", "paper_budget_K1000_T50_N100")):
         e = extra.get(key)
         if e:
             out[name] = {"us_per_step": round(e["us_per_step"], 2), "steps_per_s": round(e["steps_per_s"], 1)}

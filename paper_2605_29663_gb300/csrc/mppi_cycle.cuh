@@ -380,6 +380,7 @@ constexpr int kSortRegs = 4;   // points per thread kept in registers (clouds of
 struct SortSmem {
     int cnt[kSortCells + 1];
     float red[4][kSortThreads / 32];
+    float box[4];
     int part[kSortThreads / 32];
 };
 
@@ -428,11 +429,16 @@ __device__ __forceinline__ void sort_cloud_block(const float2 *__restrict__ pts,
     if (lane == 0) { sm.red[0][warp] = lx; sm.red[1][warp] = ly; sm.red[2][warp] = hx; sm.red[3][warp] = hy; }
     for (int c = tid; c <= kSortCells; c += nt) sm.cnt[c] = 0;
     __syncthreads();
-    lx = ly = finf(); hx = hy = -finf();
-    for (int w = 0; w < nw; ++w) {
-        lx = fminf(lx, sm.red[0][w]); ly = fminf(ly, sm.red[1][w]);
-        hx = fmaxf(hx, sm.red[2][w]); hy = fmaxf(hy, sm.red[3][w]);
+    if (warp == 0) {   // the warps' boxes, reduced by one warp
+        const bool w = lane < nw;
+        lx = warp_min_f(w ? sm.red[0][lane] : finf());
+        ly = warp_min_f(w ? sm.red[1][lane] : finf());
+        hx = -warp_min_f(w ? -sm.red[2][lane] : finf());
+        hy = -warp_min_f(w ? -sm.red[3][lane] : finf());
+        if (lane == 0) { sm.box[0] = lx; sm.box[1] = ly; sm.box[2] = hx; sm.box[3] = hy; }
     }
+    __syncthreads();
+    lx = sm.box[0]; ly = sm.box[1]; hx = sm.box[2]; hy = sm.box[3];
     const float sx = 64.f / fmaxf(hx - lx, 1e-6f), sy = 64.f / fmaxf(hy - ly, 1e-6f);
     auto cell_of = [&](bool ok, float2 p) -> int {
         if (!ok) return kSortCells;
@@ -466,8 +472,19 @@ __device__ __forceinline__ void sort_cloud_block(const float2 *__restrict__ pts,
     }
     if (lane == 31) sm.part[warp] = inc;
     __syncthreads();
-    int base = 0;
-    for (int w = 0; w < warp; ++w) base += sm.part[w];
+    if (warp == 0) {   // exclusive prefix of the warps' totals, by one warp
+        const int v = lane < nw ? sm.part[lane] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        __syncwarp();
+        if (lane < nw) sm.part[lane] = x - v;
+    }
+    __syncthreads();
+    const int base = sm.part[warp];
     int run = base + inc - s;
     for (int c = c0; c < c1; ++c) {
         const int v = sm.cnt[c];

@@ -166,6 +166,20 @@ def plain_step(seed=0, K=256, T=20, N=512) -> dict:
                 kind=POLYGON, fp=l_footprint(), params=mppi_params(K, T, DIFF))
 
 
+def paper_budget(seed=0, K=1000, T=50, N=100) -> dict:
+    """The paper's navigation sampling budget (Sec. V-A: K = 1000, T = 50,
+    dt = 0.1, N = 100 obstacle points) with the 8-vertex T-shaped body of the
+    rectangle-cover comparison; diff-drive, points uniform in [-4, 4]^2
+    outside a 1.5 m disc, goal 5 m ahead, the plain step's noise."""
+    g = rng(seed)
+    return dict(q0=np.zeros(3, dtype=np.float32),
+                cloud=ring_excluded_points(g, N, 4.0, 1.5), mask=None,
+                waypoints=np.array([[5.0, 0.0]], dtype=np.float32),
+                U=np.zeros((T, 2), dtype=np.float32),
+                eps=noise(g, K, T, (0.3, 0.6)),
+                kind=POLYGON, fp=rectilinear_shapes()["T"][0].astype(np.float32), params=mppi_params(K, T, DIFF))
+
+
 def forklift(seed=0, K=2048, T=40, N=4096) -> dict:
     g = rng(seed)
     xs = np.arange(-2.0, 14.0, 0.01)

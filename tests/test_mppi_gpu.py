@@ -101,6 +101,14 @@ def test_plain_step_full_size(ex, ctx):
     compare(s, run_gpu(ex, ctx, s), o)
 
 
+def test_paper_budget_full_size(ex, ctx):
+    """The paper's sampling budget (K=1000, T=50, N=100, 8-edge T body) in the
+    launch the benchmark times (no d_min output: point-level pruning, two
+    samples per block), against the oracle."""
+    s, o = _seeded(lambda k: synth.paper_budget(k), 0)
+    compare(s, run_gpu(ex, ctx, s, dmin=False), o, check_dmin=False)
+
+
 @pytest.mark.parametrize("model", [synth.DIFF, synth.ACKERMANN, synth.OMNI, synth.SPIN, synth.PARALLEL])
 def test_motion_models(ex, ctx, model):
     def make(seed):
