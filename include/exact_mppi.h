@@ -185,10 +185,13 @@ typedef struct {
  *   valid     device, 1 int32, or NULL: 1 if the updated nominal passed
  *   U_upd     device, T x n_u, or NULL: the updated nominal before shift/reset
  *   dmin      device, K x T, or NULL: d_min of every scored rollout state.
- *             Without it the sample phase skips point sub-chunks that cannot
- *             come within d_safe of the footprint at a step: every cost term
- *             and the validation test are the same for any d >= d_safe, so
- *             costs, weights and U are identical either way
+ *             Without it the sample phase skips the points that provably
+ *             cannot come within d_safe of the footprint at a step (bounding
+ *             circles of point sub-chunks, then the footprint's bounding box
+ *             for the points or 16-point fine sub-chunks of the kept ones;
+ *             below 1,024 points, bounding circles per point): every cost
+ *             term and the validation test are the same for any d >= d_safe,
+ *             so costs, weights and U are identical either way
  * Limits: 1 <= K <= 65536, 1 <= T <= 128, n_points >= 0, n_wp >= 1,
  * n_u must match the model.  Scratch comes from ctx (grown on demand). */
 int mppi_step(exact_ctx *ctx, const float *state, const float *cloud, const uint8_t *mask,
