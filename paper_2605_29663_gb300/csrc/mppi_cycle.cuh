@@ -677,27 +677,25 @@ __device__ __forceinline__ void steps_min_keys(const EV &ev, const float2 *pts, 
                     best = fmin3(best, k[0], k[1]);
                     if (two) best = fmin3(best, k[2], k[3]);
                 }
-                best = warp_min_f(best);
-                if (lane == 0) atomicMin(keyh + h, f2ord(best));
-                continue;
-            }
-            for (int j = c * span + lane; j < jend; j += 32) {
-                float2 o0, o1;
-                if constexpr (MOVING) {
-                    const float4 *p4 = reinterpret_cast<const float4 *>(pts);
-                    const float4 a0 = p4[2 * j], a1 = p4[min(2 * j + 1, n - 1)];
-                    o0 = make_float2(fmaf(th, a0.z, a0.x), fmaf(th, a0.w, a0.y));
-                    o1 = make_float2(fmaf(th, a1.z, a1.x), fmaf(th, a1.w, a1.y));
-                } else {
-                    o0 = pts[2 * j];
-                    o1 = pts[min(2 * j + 1, n - 1)];
+            } else {
+                for (int j = c * span + lane; j < jend; j += 32) {
+                    float2 o0, o1;
+                    if constexpr (MOVING) {
+                        const float4 *p4 = reinterpret_cast<const float4 *>(pts);
+                        const float4 a0 = p4[2 * j], a1 = p4[min(2 * j + 1, n - 1)];
+                        o0 = make_float2(fmaf(th, a0.z, a0.x), fmaf(th, a0.w, a0.y));
+                        o1 = make_float2(fmaf(th, a1.z, a1.x), fmaf(th, a1.w, a1.y));
+                    } else {
+                        o0 = pts[2 * j];
+                        o1 = pts[min(2 * j + 1, n - 1)];
+                    }
+                    float px0, py0, px1, py1;
+                    body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
+                    body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
+                    float k0, k1;
+                    ev.eval2(px0, py0, px1, py1, k0, k1);
+                    best = fmin3(best, k0, k1);
                 }
-                float px0, py0, px1, py1;
-                body_frame(o0.x, o0.y, q.x, q.y, q.z, q.w, px0, py0);
-                body_frame(o1.x, o1.y, q.x, q.y, q.z, q.w, px1, py1);
-                float k0, k1;
-                ev.eval2(px0, py0, px1, py1, k0, k1);
-                best = fmin3(best, k0, k1);
             }
             best = warp_min_f(best);
             if (lane == 0) atomicMin(keyh + h, f2ord(best));
