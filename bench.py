@@ -50,7 +50,7 @@ L2_BYTES = 129 * 1024 * 1024
 # null otherwise).
 TRAFFIC = {"sources": ["paper_2605_29663_gb300/csrc/sdf_batch.cu", "paper_2605_29663_gb300/csrc/common.cuh",
                        "paper_2605_29663_gb300/csrc/internal.h"],
-           "sha256_16": "1169cca8386141bc", "bytes_per_launch": 444672 + 478292992}
+           "sha256_16": "ee1107a292ea716e", "bytes_per_launch": 632832 + 477973248}
 
 
 def measured_traffic():
