@@ -329,6 +329,14 @@ def stage_cost(world: World, u: np.ndarray, d: np.ndarray, p: dict) -> np.ndarra
             + np.where(d < 0, p["w_coll"], 0.0) + p["w_rep"] * gap ** 2)
 
 
+def collided_remainder(cost: np.ndarray, collided: np.ndarray, t_coll: np.ndarray, goal_dist: np.ndarray,
+                       max_steps: int, w_goal: float) -> np.ndarray:
+    """Final trajectory costs: a collided robot stays where it collided and
+    pays w_goal * (its distance to the goal) for every step of the episode it
+    did not run (max_steps - t_coll); other episodes keep their costs."""
+    return cost + np.where(collided, w_goal * goal_dist * (max_steps - t_coll), 0.0)
+
+
 def generate_dataset(torch, dev, n_samples: int, n_envs: int, K: int, seed: int, log=print):
     """Closed-loop plain MPPI (K samples) in n_envs worlds; returns device
     tensors X (n x D_IN) features and Y (n x 2T) = U_upd - U_prev."""
@@ -451,8 +459,7 @@ def evaluate(torch, dev, method: str, K: int, n_episodes: int, seed: int, mlp: M
         active &= ~(newly_coll | reached)
         if not active.any():
             break
-    # a collided robot stays where it collided: the goal term for every step it did not run
-    cost += np.where(collided, p["w_goal"] * world.goal_dist() * (max_steps - t_coll), 0.0)
+    cost = collided_remainder(cost, collided, t_coll, world.goal_dist(), max_steps, p["w_goal"])
     ci = 1.96 * cost.std(ddof=1) / math.sqrt(n_episodes)
     progress = np.hypot(world.goal[:, 0], world.goal[:, 1]) - world.goal_dist()
     res = {"method": method, "K": K, "episodes": n_episodes, "cost_mean": float(cost.mean()), "cost_ci95": float(ci),
