@@ -3,8 +3,11 @@
 // and the batched persistent kernels (batched.cu):
 //   sample_body    one sample r: rollout, every (step, point) body-frame
 //                  signed distance, per-step minima, J~ (Sec. III-E, IV-C..E);
-//                  point sub-chunks that cannot come within d_safe of the
-//                  footprint are skipped when no d_min output is wanted
+//                  when no d_min output is wanted, points that cannot come
+//                  within d_safe of the footprint are skipped (sub-chunk
+//                  circles, then the footprint's bounding box per point or
+//                  per 16-point fine sub-chunk; per-point circles for small
+//                  clouds)
 //   update_body    one chunk of samples: weights and weighted clipped noise
 //                  into a partial slot (Alg. 1 step 3)
 //   validate_body  one (step, point chunk) of the nominal: adds the partial
