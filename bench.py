@@ -912,14 +912,28 @@ def run_gpu(args):
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if not args.no_extra and world == 1:
-        line["extra"] = mppi_extra(torch, ex, dev, cpu=not args.no_cpu)
-        line["extra"]["batched64"] = batched_extra(torch, ex, dev)
-        line["extra"]["batched_small128"] = batched_small_extra(torch, ex, dev)
-        line["extra"]["hybrid3"] = hybrid_extra(torch, ex, dev, cpu=not args.no_cpu)
-        line["extra"]["predicted"] = predicted_extra(torch, ex, dev, cpu=not args.no_cpu)
-        line["extra"].update(sdf_extra(torch, ex, dev))
-        line["extra"]["learned"] = learned_extra(torch, ex, dev)
-        line["mppi"] = mppi_summary(line["extra"])   # last key: short enough to survive a truncated tail
+        # the headline above is complete; a failing extra measurement is
+        # recorded in extra_errors instead of losing the line
+        errors = {}
+
+        def guarded(name, fn):
+            try:
+                return fn()
+            except Exception as e:
+                errors[name] = f"{type(e).__name__}: {e}"[:300]
+                return None
+        extra = guarded("mppi", lambda: mppi_extra(torch, ex, dev, cpu=not args.no_cpu)) or {}
+        for name, fn in (("batched64", lambda: batched_extra(torch, ex, dev)),
+                         ("batched_small128", lambda: batched_small_extra(torch, ex, dev)),
+                         ("hybrid3", lambda: hybrid_extra(torch, ex, dev, cpu=not args.no_cpu)),
+                         ("predicted", lambda: predicted_extra(torch, ex, dev, cpu=not args.no_cpu))):
+            extra[name] = guarded(name, fn)
+        extra.update(guarded("sdf_extra", lambda: sdf_extra(torch, ex, dev)) or {})
+        extra["learned"] = guarded("learned", lambda: learned_extra(torch, ex, dev))
+        line["extra"] = extra
+        if errors:
+            line["extra_errors"] = errors
+        line["mppi"] = mppi_summary(extra)   # last key: short enough to survive a truncated tail
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
